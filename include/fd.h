@@ -1,0 +1,247 @@
+/*
+ * fd.h -- C ABI of the GB300 filter-diagonalization (FD) library.
+ *
+ * Filter diagonalization (Alvermann, Hager, Fehske, arXiv 2209.01974) finds
+ * the N_t eigenpairs of a large sparse symmetric matrix H nearest a target
+ * window by repeatedly applying a Chebyshev polynomial filter to a block of
+ * N_s search vectors (Sec. 2, Alg. 1 and Alg. 2), orthonormalising the block,
+ * and extracting Ritz pairs with one more sparse matrix-multiple-vector
+ * product (SpMMV).  This header exposes the steps of that hot path:
+ *
+ *   fd_build_matrix / fd_matrix_from_csr   -> on-device SELL-C-sigma matrix
+ *   fd_spectral_bounds                     -> inclusion interval (Sec. 2)
+ *   fd_filter                              -> V <- p(alpha H + beta) V (Alg. 2)
+ *   fd_orthonormalize                      -> Cholesky-QR of the block (Sec. 2)
+ *   fd_rayleigh_ritz                       -> Ritz pairs + residuals (Sec. 2)
+ *   fd_solve                               -> the whole FD loop (Alg. 1)
+ *   fd_kpm_moments                         -> KPM density-of-states moments (Sec. 4.1)
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns fd_status; no C++ exception crosses the ABI.  On an
+ *     error, fd_last_error(ctx) returns a message for the last failing call
+ *     made with that context.
+ *   - Blocks of vectors are caller-owned DEVICE buffers (e.g. the data
+ *     pointer of a torch tensor), row-major: element (i, j) of a D x m block
+ *     with leading dimension ld sits at p[i * ld + j], rows in the matrix's
+ *     ORIGINAL row order.  Base pointers and ld * element size must be
+ *     multiples of 16 bytes for the SpMMV kernels.
+ *   - All device work is ordered on the context's CUDA stream.  Calls that
+ *     write HOST outputs synchronise that stream before returning; the others
+ *     return after enqueueing work.
+ *   - Matrices are library-owned and freed with fd_matrix_free.
+ *   - The library allocates its internal workspaces with cudaMalloc and keeps
+ *     them in the context until fd_destroy.
+ */
+#ifndef FD_H
+#define FD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fd_ctx fd_ctx;
+typedef struct fd_matrix fd_matrix;
+
+typedef enum {
+  FD_OK = 0,
+  FD_ERR_ARG = 1,       /* invalid argument (checked before any device work) */
+  FD_ERR_CUDA = 2,      /* a CUDA runtime call or kernel launch failed */
+  FD_ERR_OOM = 3,       /* device allocation failed */
+  FD_ERR_NOCONV = 4,    /* fd_solve reached max_outer without convergence */
+  FD_ERR_BREAKDOWN = 5, /* Cholesky-QR failed even with the shift */
+  FD_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+  FD_ERR_BOUNDS = 7     /* a device-side bounds check fired (bad CSR / index) */
+} fd_status;
+
+typedef enum { FD_F64 = 0, FD_F32 = 1 } fd_prec;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`; `stream` is a cudaStream_t (NULL =
+ * the legacy default stream).  The context does not own the stream. */
+fd_status fd_create(fd_ctx** ctx, int device, void* stream);
+/* Destroy the context and free its workspaces.  Matrices must be freed first. */
+fd_status fd_destroy(fd_ctx* ctx);
+/* Replace the stream all later calls enqueue on. */
+fd_status fd_set_stream(fd_ctx* ctx, void* stream);
+/* Message of the last failing call on this context ("" if none).  The string
+ * is owned by the context and valid until its next call. */
+const char* fd_last_error(const fd_ctx* ctx);
+/* Number of kernels this context has launched since creation (for audits). */
+int64_t fd_kernel_launches(const fd_ctx* ctx);
+
+/* ------------------------------------------------------------------ matrices */
+
+/* Build a test matrix on the device from a parameter string (the paper names
+ * its matrices by ScaMaC parameter strings, Sec. 3.2; Table 2):
+ *   "hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open"     (bc = open|periodic)
+ *   "anderson3d:L=128,W=2,seed=1,t=1"   periodic cubic lattice, eps_i = W (u_i - 1/2)
+ *   "chain:n=1000,t=1"                  open tight-binding chain
+ * Generation is integer-exact and bit-identical to the CPU definition (Hubbard
+ * basis: occupation bitstrings ranked in increasing order, row = rank_up *
+ * dim_dn + rank_dn, hop sign (-1)^(fermions passed)).  The result is stored in
+ * SELL-C-sigma (Kreutzer et al. 2014, the format of the GHOST library the
+ * paper uses) with chunk height C (a multiple of 32) and sorting window
+ * sigma >= 1 (sigma = 1: no reordering).  FP64 values and an FP32 copy are
+ * kept.  Errors: FD_ERR_ARG for an unknown kind, a missing or out-of-range
+ * parameter, or D >= 2^31. */
+fd_status fd_build_matrix(fd_ctx* ctx, const char* spec, fd_matrix** out);
+fd_status fd_build_matrix_sell(fd_ctx* ctx, const char* spec, int C, int sigma,
+                               fd_matrix** out);
+
+/* Copy a symmetric CSR matrix from HOST arrays (rowptr: D+1 int64, col: nnz
+ * int32 strictly ascending per row, val: nnz double).  The arrays are copied;
+ * the caller keeps ownership.  A missing diagonal entry is stored as an
+ * explicit zero internally but not exported.  Symmetry is the caller's
+ * responsibility.  Errors: FD_ERR_ARG for a malformed rowptr, a column out of
+ * [0, D) or not ascending. */
+fd_status fd_matrix_from_csr(fd_ctx* ctx, int64_t D, const int64_t* rowptr,
+                             const int32_t* col, const double* val, int C,
+                             int sigma, fd_matrix** out);
+fd_status fd_matrix_free(fd_matrix* A);
+
+typedef struct {
+  int64_t D;          /* dimension */
+  int64_t nnz;        /* stored entries of the CSR form (diagonal included) */
+  int64_t nnz_sell;   /* SELL entries including chunk padding */
+  int64_t n_chunks;   /* number of SELL chunks */
+  int32_t C, sigma;   /* SELL chunk height and sorting window */
+  int32_t max_row;    /* longest row (SELL form, diagonal included) */
+  int32_t identity_perm; /* 1 if SELL row order equals the original order */
+  double gersh_lo, gersh_hi; /* Gershgorin inclusion interval */
+} fd_matrix_info;
+
+fd_status fd_matrix_get_info(const fd_matrix* A, fd_matrix_info* info);
+
+/* Export the matrix, reconstructed from its device SELL-C-sigma arrays, as
+ * CSR in the original row order into HOST arrays (rowptr: D+1, col and val:
+ * info.nnz).  Bit-exact with what was built or imported.  Synchronises. */
+fd_status fd_matrix_to_csr(fd_ctx* ctx, const fd_matrix* A, int64_t* rowptr,
+                           int32_t* col, double* val);
+
+/* HOST array perm[D]: SELL row i holds original row perm[i].  Synchronises. */
+fd_status fd_matrix_perm(fd_ctx* ctx, const fd_matrix* A, int64_t* perm);
+
+/* ------------------------------------------------------------------ hot path */
+
+/* Spectral inclusion interval [lam_l, lam_r] (Sec. 2, Alg. 1 steps 1-2):
+ * `steps` Lanczos steps (0 -> 20) with full reorthogonalisation from the start
+ * vector of SplitMix64 stream 3 with `seed`; each extreme Ritz value is moved
+ * outwards by its Lanczos residual bound |beta_m s_m| plus 1% of the Ritz
+ * span, then clipped to the Gershgorin interval.  Host outputs; synchronises. */
+fd_status fd_spectral_bounds(fd_ctx* ctx, const fd_matrix* A, int steps,
+                             uint64_t seed, double* lam_l, double* lam_r);
+
+/* Chebyshev filter V <- p(A~) V, p(x) = sum_{k=0..degree} mu[k] T_k(x),
+ * A~ = alpha H + beta I (Sec. 2, Alg. 2), applied to the nb columns of the
+ * D x nb block V (device, leading dimension ldv).  One fused kernel per
+ * degree step computes the SpMMV W2 <- 2 A~ W1 - W2 together with
+ * V <- V + mu_k W2 (Alg. 2 fuses the SpMV with the vector update so that W2 is
+ * not read twice).
+ *   prec    FD_F64: V, W1, W2 are double and H's FP64 values are used;
+ *           FD_F32: V, W1, W2 are float, H's FP32 copy, FP32 accumulation.
+ *   nb      2, 4, 8, 16, 32, 64 or 128 (FP64); 4 .. 128 (FP32)
+ *   degree  n >= 2 (Alg. 2 takes degree n >= 2); mu: HOST array of n+1 doubles
+ *   W1, W2  device workspaces, D x nb each with leading dimension ldw
+ *           (contents are overwritten)
+ * Errors: FD_ERR_ARG (bad nb / degree / alignment / NULL), FD_ERR_CUDA. */
+fd_status fd_filter(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, void* V,
+                    int64_t ldv, int nb, int degree, const double* mu,
+                    double alpha, double beta, void* W1, void* W2, int64_t ldw);
+
+/* Filter coefficients mu[0..n] (HOST array of n+1 doubles) of the Chebyshev
+ * expansion of the indicator of the window [x_l, x_r] (scaled coordinates,
+ * clipped to [-1, 1]) damped by the Jackson kernel, normalised so that p at
+ * the window centre is 1 (Sec. 2 expands a window function in Chebyshev
+ * polynomials; the Jackson kernel is the KPM kernel the paper cites):
+ *   c_0 = (t_l - t_r)/pi, c_k = 2 (sin k t_l - sin k t_r)/(k pi), t = arccos x
+ *   g_k = [(N-k+1) cos(pi k/(N+1)) + sin(pi k/(N+1)) cot(pi/(N+1))]/(N+1), N = n+1
+ * Pure host arithmetic.  Errors: FD_ERR_ARG for n < 2 or x_l >= x_r. */
+fd_status fd_filter_coeffs(double x_l, double x_r, int n, double* mu);
+
+/* Sparse matrix times block: Y <- H X for D x nb blocks (the extra SpMMV of
+ * Sec. 2 that precedes the Rayleigh-Ritz step).  Same layout rules as
+ * fd_filter. */
+fd_status fd_spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec,
+                   const void* X, int64_t ldx, void* Y, int64_t ldy, int nb);
+
+/* Orthonormalise the D x ns FP64 block V in place (Sec. 2: orthogonalisation
+ * after the random start and after every filter application) by Cholesky-QR
+ * twice (G = V^T V, G = R^T R, V <- V R^-1).  A Cholesky pivot that is not
+ * > 0 makes that pass use G + s I with s = 11 (D ns + ns (ns+1)) 2^-53 tr(G)
+ * (shifted Cholesky-QR, Fukaya et al. 2020) and adds a third pass.
+ *   R       optional DEVICE ns x ns row-major output of the upper factor with
+ *           V_in = V_out R (NULL = not returned)
+ *   passes  optional HOST output: number of passes run (2 or 3)
+ * Synchronises (one pivot check per pass).  Errors: FD_ERR_ARG,
+ * FD_ERR_BREAKDOWN (the shifted factorisation failed too, e.g. NaN input). */
+fd_status fd_orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns,
+                            int64_t ldv, double* R, int* passes);
+
+/* Rayleigh-Ritz step (Sec. 2): for an orthonormal D x ns FP64 block V,
+ * AV <- H V, Hs = V^T AV, Hs = Q diag(theta) Q^T (theta ascending, FP64
+ * Jacobi on the device), V <- V Q, AV <- AV Q and resid_i = ||AV_i -
+ * theta_i V_i||_2.  V and AV share the leading dimension ld.  theta and resid
+ * are HOST arrays of ns doubles.  Synchronises. */
+fd_status fd_rayleigh_ritz(fd_ctx* ctx, const fd_matrix* A, double* V,
+                           double* AV, int64_t D, int ns, int64_t ld,
+                           double* theta, double* resid);
+
+/* Parameters of the FD loop; zero fields take the defaults in brackets. */
+typedef struct {
+  int ns;            /* search vectors N_s [nb * ceil(4 N_t / nb)] (Sec. 2: N_s/N_t ~ 4) */
+  int max_outer;     /* outer iterations before FD_ERR_NOCONV [60] */
+  int n_max;         /* largest filter degree [100000] */
+  int lanczos_steps; /* [20] */
+  uint64_t seed;     /* start block: SplitMix64 stream 2 (Lanczos: stream 3) [0] */
+  int precision;     /* FD_F64: all-FP64 sweeps; FD_F32: FP32 sweeps until the
+                        FP32 floor, then FP64 sweeps [FD_F64] */
+  double c_n;        /* degree = c_n pi / dtheta [4] */
+  double m_l, m_r;   /* window edge = target edge + m (search edge - target edge) [0.5] */
+  int verbose;       /* 1: print one line per outer iteration to stderr */
+} fd_options;
+
+typedef struct {
+  int converged;       /* 1 if all N_t residuals <= tol */
+  int iterations;      /* outer iterations (Rayleigh-Ritz steps) */
+  int64_t n_spmmv;     /* SpMMVs applied to the full N_s-column block */
+  int64_t n_spmmv_f32; /* of which FP32 */
+  int final_degree;
+  int ns;
+  double lam_l, lam_r; /* inclusion interval used last */
+  double window_l, window_r;
+  double t_total, t_bounds, t_filter, t_ortho, t_rr; /* seconds (CUDA events) */
+  double filter_bytes; /* algorithmic bytes of all filter steps (kappa = 5) */
+} fd_result;
+
+/* Filter diagonalization (Sec. 2, Alg. 1): the n_target eigenpairs of H
+ * nearest the centre of the window [a, b] to residual ||H x - theta x||_2 <=
+ * tol.  `degree` is the first and smallest filter degree; later degrees and
+ * the target/search intervals follow the Ritz-value heuristic of fd_options
+ * (the paper's Lehmann intervals are not used).
+ *   theta, resid  HOST arrays of n_target doubles (ascending theta)
+ *   X             optional DEVICE D x n_target FP64 row-major eigenvectors
+ *                 (largest-magnitude entry positive), or NULL
+ * Returns FD_ERR_NOCONV (with the outputs filled) if max_outer is reached. */
+fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b,
+                   int n_target, int nb, int degree, double tol,
+                   const fd_options* opt, fd_result* res, double* theta,
+                   double* resid, double* X, int64_t ldx);
+
+/* Kernel-polynomial moments mu_m = (1/(R D)) sum_r r^T T_m(A~) r, m <
+ * n_moments, with R = n_random normal-like random vectors (SplitMix64 stream
+ * 4, `seed`) and A~ = alpha H + beta I (Sec. 4.1 computes the DOS with KPM).
+ * n_random in {2, 4, 8, 16, 32, 64}; mu is a HOST array of n_moments doubles.
+ * Synchronises. */
+fd_status fd_kpm_moments(fd_ctx* ctx, const fd_matrix* A, int n_moments,
+                         int n_random, uint64_t seed, double alpha, double beta,
+                         double* mu);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FD_H */

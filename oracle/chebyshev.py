@@ -3,8 +3,8 @@
 The filter is p(x) = sum_{k=0..n} mu_k T_k(x) on the scaled matrix
 A~ = alpha A + beta I, where alpha, beta map the spectral inclusion interval
 [lam_l, lam_r] onto [-1, 1] (Sec. 2).  The coefficients are the Chebyshev
-expansion of the indicator of a window [x_l, x_r] (Sec. 2: "Chebyshev
-expansion of a window function"), damped by the Jackson kernel (the kernel
+expansion of the indicator of a window [x_l, x_r] (Sec. 2 builds the filter
+from the Chebyshev series of a window function), damped by the Jackson kernel (the kernel
 polynomial method the paper cites for KPM, Sec. 4.1):
 
     theta = arccos(x)

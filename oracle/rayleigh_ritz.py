@@ -1,5 +1,6 @@
-"""Rayleigh-Ritz step and residual norms (Sec. 2, Alg. 1: "a single additional
-SpMV provides the Ritz values"; residual rho = ||A v - lambda v||_2).
+"""Rayleigh-Ritz step and residual norms (Sec. 2, Alg. 1: after each
+orthogonalisation one more SpMV yields the Ritz values; the convergence test
+uses the residual rho = ||A v - lambda v||_2).
 
 For an orthonormal D x N_s block V:
     W = A V ;  H = V^T W, symmetrised (H + H^T)/2 ;  H = Q diag(theta) Q^T

@@ -5,8 +5,8 @@ generators", OOPSLA 2014 (the ``mix64`` finaliser with constants
 0xbf58476d1ce4e5b9 / 0x94d049bb133111eb and the golden gamma
 0x9e3779b97f4a7c15).  The FD method draws random numbers in three places --
 the on-site disorder of the Anderson matrices, the random start block of FD
-(Sec. 2, "initial assignment of random vectors") and the Lanczos start vector
-(Sec. 2, "a few steps of the Lanczos algorithm") -- and these draws happen
+(Sec. 2: FD starts from random search vectors) and the Lanczos start vector
+(Sec. 2: the inclusion interval comes from a short Lanczos run) -- and these draws happen
 inside the library, so each side implements this generator on its own:
 
     key(seed, stream) = mix64(seed XOR mix64(stream))

@@ -1,0 +1,300 @@
+"""Python binding of libfd, the GB300 filter-diagonalization library.
+
+Argument marshalling only: every step of the FD hot path runs in the CUDA
+kernels of ``libfd.so`` (built by ``paper_2209_01974_gb300.build``).  Device
+blocks are torch CUDA tensors (row-major, unit column stride, leading
+dimension = ``stride(0)``); host outputs are NumPy arrays.  The functions keep
+the names of the C ABI in ``include/fd.h``.  There is no fallback: if the
+library is missing, importing the binding raises ``ImportError``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run paper_2209_01974_gb300.build.build() "
+                      "(or __graft_entry__.build()) first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FD_OK, FD_ERR_ARG, FD_ERR_CUDA, FD_ERR_OOM, FD_ERR_NOCONV, FD_ERR_BREAKDOWN, FD_ERR_TIMEOUT, \
+    FD_ERR_BOUNDS = range(8)
+FD_F64, FD_F32 = 0, 1
+STATUS_NAMES = {0: "FD_OK", 1: "FD_ERR_ARG", 2: "FD_ERR_CUDA", 3: "FD_ERR_OOM", 4: "FD_ERR_NOCONV",
+                5: "FD_ERR_BREAKDOWN", 6: "FD_ERR_TIMEOUT", 7: "FD_ERR_BOUNDS"}
+
+_vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+_pd = ctypes.POINTER(ctypes.c_double)
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+_pi32 = ctypes.POINTER(ctypes.c_int32)
+
+
+class fd_matrix_info(ctypes.Structure):
+    _fields_ = [("D", _i64), ("nnz", _i64), ("nnz_sell", _i64), ("n_chunks", _i64),
+                ("C", ctypes.c_int32), ("sigma", ctypes.c_int32), ("max_row", ctypes.c_int32),
+                ("identity_perm", ctypes.c_int32), ("gersh_lo", _dbl), ("gersh_hi", _dbl)]
+
+
+class fd_options(ctypes.Structure):
+    _fields_ = [("ns", _i32), ("max_outer", _i32), ("n_max", _i32), ("lanczos_steps", _i32),
+                ("seed", ctypes.c_uint64), ("precision", _i32), ("c_n", _dbl), ("m_l", _dbl),
+                ("m_r", _dbl), ("verbose", _i32)]
+
+
+class fd_result(ctypes.Structure):
+    _fields_ = [("converged", _i32), ("iterations", _i32), ("n_spmmv", _i64),
+                ("n_spmmv_f32", _i64), ("final_degree", _i32), ("ns", _i32), ("lam_l", _dbl),
+                ("lam_r", _dbl), ("window_l", _dbl), ("window_r", _dbl), ("t_total", _dbl),
+                ("t_bounds", _dbl), ("t_filter", _dbl), ("t_ortho", _dbl), ("t_rr", _dbl),
+                ("filter_bytes", _dbl)]
+
+
+_SIGS = {
+    "fd_create": (_i32, [ctypes.POINTER(_vp), _i32, _vp]),
+    "fd_destroy": (_i32, [_vp]),
+    "fd_set_stream": (_i32, [_vp, _vp]),
+    "fd_last_error": (ctypes.c_char_p, [_vp]),
+    "fd_kernel_launches": (_i64, [_vp]),
+    "fd_build_matrix": (_i32, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)]),
+    "fd_build_matrix_sell": (_i32, [_vp, ctypes.c_char_p, _i32, _i32, ctypes.POINTER(_vp)]),
+    "fd_matrix_from_csr": (_i32, [_vp, _i64, _pi64, _pi32, _pd, _i32, _i32, ctypes.POINTER(_vp)]),
+    "fd_matrix_free": (_i32, [_vp]),
+    "fd_matrix_get_info": (_i32, [_vp, ctypes.POINTER(fd_matrix_info)]),
+    "fd_matrix_to_csr": (_i32, [_vp, _vp, _pi64, _pi32, _pd]),
+    "fd_matrix_perm": (_i32, [_vp, _vp, _pi64]),
+    "fd_spectral_bounds": (_i32, [_vp, _vp, _i32, ctypes.c_uint64, _pd, _pd]),
+    "fd_filter": (_i32, [_vp, _vp, _i32, _vp, _i64, _i32, _i32, _pd, _dbl, _dbl, _vp, _vp, _i64]),
+    "fd_filter_coeffs": (_i32, [_dbl, _dbl, _i32, _pd]),
+    "fd_spmmv": (_i32, [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _i32]),
+    "fd_orthonormalize": (_i32, [_vp, _vp, _i64, _i32, _i64, _vp, ctypes.POINTER(_i32)]),
+    "fd_rayleigh_ritz": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, _i64, _pd, _pd]),
+    "fd_solve": (_i32, [_vp, _vp, _dbl, _dbl, _i32, _i32, _i32, _dbl, ctypes.POINTER(fd_options),
+                        ctypes.POINTER(fd_result), _pd, _pd, _vp, _i64]),
+    "fd_kpm_moments": (_i32, [_vp, _vp, _i32, _i32, ctypes.c_uint64, _dbl, _dbl, _pd]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = sorted(_SIGS)
+
+
+class FDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(ctx, status):
+    if status != FD_OK:
+        msg = _lib.fd_last_error(ctx.handle if ctx is not None else None)
+        raise FDError(status, msg.decode() if msg else "")
+
+
+def _dptr(a, dtype):
+    return a.ctypes.data_as(ctypes.POINTER(dtype))
+
+
+def _block(t, name):
+    """(pointer, ld, D, ncols, prec) of a row-major CUDA tensor block."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D CUDA tensor")
+    if t.stride(1) != 1:
+        raise ValueError(f"{name} must have unit column stride")
+    if t.dtype == torch.float64:
+        prec = FD_F64
+    elif t.dtype == torch.float32:
+        prec = FD_F32
+    else:
+        raise ValueError(f"{name} must be float64 or float32")
+    return t.data_ptr(), t.stride(0), t.shape[0], t.shape[1], prec
+
+
+class Ctx:
+    def __init__(self, device=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = _vp()
+        st = _lib.fd_create(ctypes.byref(h), device, _vp(stream))
+        if st != FD_OK:
+            raise FDError(st, f"fd_create(device={device}) failed")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _lib.fd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def kernel_launches(self):
+        return _lib.fd_kernel_launches(self.handle)
+
+
+class Matrix:
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def free(self):
+        if self.handle:
+            _lib.fd_matrix_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def info(self):
+        inf = fd_matrix_info()
+        _check(self.ctx, _lib.fd_matrix_get_info(self.handle, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in fd_matrix_info._fields_}
+
+    @property
+    def D(self):
+        return self.info["D"]
+
+
+def fd_create(device=0, stream=None):
+    return Ctx(device, stream)
+
+
+def fd_set_stream(ctx, stream):
+    _check(ctx, _lib.fd_set_stream(ctx.handle, _vp(stream)))
+
+
+def fd_build_matrix(ctx, spec, C=32, sigma=1):
+    h = _vp()
+    _check(ctx, _lib.fd_build_matrix_sell(ctx.handle, spec.encode(), C, sigma, ctypes.byref(h)))
+    return Matrix(ctx, h)
+
+
+def fd_matrix_from_csr(ctx, rowptr, col, val, C=32, sigma=1):
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    h = _vp()
+    _check(ctx, _lib.fd_matrix_from_csr(ctx.handle, len(rowptr) - 1, _dptr(rowptr, ctypes.c_int64),
+                                        _dptr(col, ctypes.c_int32), _dptr(val, ctypes.c_double),
+                                        C, sigma, ctypes.byref(h)))
+    return Matrix(ctx, h)
+
+
+def fd_matrix_to_csr(ctx, A):
+    inf = A.info
+    rowptr = np.empty(inf["D"] + 1, dtype=np.int64)
+    col = np.empty(max(1, inf["nnz"]), dtype=np.int32)
+    val = np.empty(max(1, inf["nnz"]), dtype=np.float64)
+    _check(ctx, _lib.fd_matrix_to_csr(ctx.handle, A.handle, _dptr(rowptr, ctypes.c_int64),
+                                      _dptr(col, ctypes.c_int32), _dptr(val, ctypes.c_double)))
+    return rowptr, col[:inf["nnz"]], val[:inf["nnz"]]
+
+
+def fd_matrix_perm(ctx, A):
+    perm = np.empty(A.D, dtype=np.int64)
+    _check(ctx, _lib.fd_matrix_perm(ctx.handle, A.handle, _dptr(perm, ctypes.c_int64)))
+    return perm
+
+
+def fd_spectral_bounds(ctx, A, steps=20, seed=0):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, _lib.fd_spectral_bounds(ctx.handle, A.handle, steps, seed, ctypes.byref(lo),
+                                        ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def fd_filter(ctx, A, V, mu, alpha, beta, W1, W2):
+    """V <- p(alpha A + beta) V in place; W1, W2: workspaces of V's shape and dtype."""
+    pv, ldv, D, nb, prec = _block(V, "V")
+    p1, ldw, _, _, prec1 = _block(W1, "W1")
+    p2, ldw2, _, _, prec2 = _block(W2, "W2")
+    if ldw != ldw2 or prec1 != prec or prec2 != prec:
+        raise ValueError("W1 and W2 need the same leading dimension and V's dtype")
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    _check(ctx, _lib.fd_filter(ctx.handle, A.handle, prec, _vp(pv), ldv, nb, len(mu) - 1,
+                               _dptr(mu, ctypes.c_double), alpha, beta, _vp(p1), _vp(p2), ldw))
+
+
+def fd_filter_coeffs(x_l, x_r, n):
+    mu = np.empty(n + 1)
+    st = _lib.fd_filter_coeffs(x_l, x_r, n, _dptr(mu, ctypes.c_double))
+    if st != FD_OK:
+        raise FDError(st, "fd_filter_coeffs: need n >= 2 and x_l < x_r")
+    return mu
+
+
+def fd_spmmv(ctx, A, X, Y):
+    px, ldx, D, nb, prec = _block(X, "X")
+    py, ldy, _, _, precy = _block(Y, "Y")
+    if precy != prec:
+        raise ValueError("X and Y must have the same dtype")
+    _check(ctx, _lib.fd_spmmv(ctx.handle, A.handle, prec, _vp(px), ldx, _vp(py), ldy, nb))
+
+
+def fd_orthonormalize(ctx, V, R=None):
+    """In-place Cholesky-QR of the FP64 block V; returns the number of passes."""
+    pv, ldv, D, ns, prec = _block(V, "V")
+    if prec != FD_F64:
+        raise ValueError("fd_orthonormalize works on float64 blocks")
+    passes = ctypes.c_int()
+    _check(ctx, _lib.fd_orthonormalize(ctx.handle, _vp(pv), D, ns, ldv,
+                                       _vp(R.data_ptr() if R is not None else None),
+                                       ctypes.byref(passes)))
+    return passes.value
+
+
+def fd_rayleigh_ritz(ctx, A, V, AV):
+    pv, ld, D, ns, prec = _block(V, "V")
+    pa, lda, _, _, _ = _block(AV, "AV")
+    if lda != ld or prec != FD_F64:
+        raise ValueError("V and AV must be float64 with the same leading dimension")
+    theta = np.empty(ns)
+    resid = np.empty(ns)
+    _check(ctx, _lib.fd_rayleigh_ritz(ctx.handle, A.handle, _vp(pv), _vp(pa), D, ns, ld,
+                                      _dptr(theta, ctypes.c_double), _dptr(resid, ctypes.c_double)))
+    return theta, resid
+
+
+def fd_solve(ctx, A, a, b, n_target, nb, degree, tol, X=None, raise_noconv=True, **opts):
+    """Filter diagonalization; returns (theta, resid, result dict).  X: optional
+    CUDA float64 tensor (D x n_target) that receives the eigenvectors."""
+    o = fd_options()
+    for k, v in opts.items():
+        if k == "precision" and isinstance(v, str):
+            v = FD_F32 if v in ("f32", "fp32", "float32") else FD_F64
+        setattr(o, k, v)
+    res = fd_result()
+    theta = np.empty(n_target)
+    resid = np.empty(n_target)
+    px, ldx = (None, 0)
+    if X is not None:
+        px, ldx, _, _, _ = _block(X, "X")
+    st = _lib.fd_solve(ctx.handle, A.handle, a, b, n_target, nb, degree, tol, ctypes.byref(o),
+                       ctypes.byref(res), _dptr(theta, ctypes.c_double), _dptr(resid, ctypes.c_double),
+                       _vp(px), ldx)
+    if st != FD_OK and not (st == FD_ERR_NOCONV and not raise_noconv):
+        _check(ctx, st)
+    return theta, resid, {k: getattr(res, k) for k, _ in fd_result._fields_}
+
+
+def fd_kpm_moments(ctx, A, n_moments, n_random, seed, alpha, beta):
+    mu = np.empty(n_moments)
+    _check(ctx, _lib.fd_kpm_moments(ctx.handle, A.handle, n_moments, n_random, seed, alpha, beta,
+                                    _dptr(mu, ctypes.c_double)))
+    return mu
