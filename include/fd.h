@@ -80,6 +80,11 @@ int64_t fd_kernel_launches(const fd_ctx* ctx);
  *   "hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open"     (bc = open|periodic)
  *   "anderson3d:L=128,W=2,seed=1,t=1"   periodic cubic lattice, eps_i = W (u_i - 1/2)
  *   "chain:n=1000,t=1"                  open tight-binding chain
+ *   "roadgraph:side=2000,q=0.3,seed=0"  Laplacian of a road-like planar graph on a
+ *                                       side x side grid: a random spanning tree
+ *                                       (each node links to its left or lower
+ *                                       neighbour) plus every other grid edge with
+ *                                       probability q (mean degree ~ 2(1+q))
  * Generation is integer-exact and bit-identical to the CPU definition (Hubbard
  * basis: occupation bitstrings ranked in increasing order, row = rank_up *
  * dim_dn + rank_dn, hop sign (-1)^(fermions passed)).  The result is stored in
@@ -202,6 +207,7 @@ typedef struct {
   double c_n;        /* degree = c_n pi / dtheta [4] */
   double m_l, m_r;   /* window edge = target edge + m (search edge - target edge) [0.5] */
   int verbose;       /* 1: print one line per outer iteration to stderr */
+  int cta_warps;     /* batched filter: warps per CTA (4 or 8) [8] */
 } fd_options;
 
 typedef struct {
@@ -215,6 +221,7 @@ typedef struct {
   double window_l, window_r;
   double t_total, t_bounds, t_filter, t_ortho, t_rr; /* seconds (CUDA events) */
   double filter_bytes; /* algorithmic bytes of all filter steps (kappa = 5) */
+  int used_graph;      /* fd_solve_batched: 1 if the iterations ran as a CUDA graph */
 } fd_result;
 
 /* Filter diagonalization (Sec. 2, Alg. 1): the n_target eigenpairs of H
@@ -231,6 +238,43 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b,
                    const fd_options* opt, fd_result* res, double* theta,
                    double* resid, double* X, int64_t ldx);
 
+/* One problem of a batch: the window [a, b], the number of wanted pairs, and
+ * the seed of its start block and Lanczos vector. */
+typedef struct {
+  double a, b;
+  int n_target;
+  uint64_t seed;
+} fd_problem;
+
+/* Filter diagonalization of n_inst independent problems at once (Alg. 1 per
+ * instance, instances of different sizes).  Each outer iteration of all
+ * unconverged instances runs as one CUDA graph: one persistent cooperative
+ * kernel applies the Chebyshev filters of every bundle of every instance (all
+ * degree steps, a grid-wide barrier between steps), batched Cholesky-QR and
+ * Rayleigh-Ritz kernels cover all instances per launch, and all Ritz values
+ * and residuals are copied to the host once.  Instances drop out when they
+ * converge.  The per-instance intervals and degrees follow fd_solve's
+ * heuristic.  Matrices must be built with sigma = 1; N_s per instance (opt->ns
+ * or nb ceil(4 n_target / nb)) must be at most 96; nb in {2, ..., 64}.
+ *   res         n_inst results
+ *   theta/resid HOST arrays holding sum(n_target) doubles, instance after
+ *               instance, ascending theta within an instance (NaN/inf for an
+ *               instance that did not converge)
+ * Returns FD_ERR_NOCONV if any instance failed to converge in max_outer. */
+fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
+                           const fd_problem* prob, int nb, int degree, double tol,
+                           const fd_options* opt, fd_result* res, double* theta,
+                           double* resid);
+
+/* Autotuner of the batched filter: for the matrices given by n_inst spec
+ * strings, times the persistent batched filter (degree `probe_degree`, FP64)
+ * for every combination of block width nb in {8, 16, 32, 64} (with N_s =
+ * nb ceil(4 n_target / nb) <= 96), SELL chunk height C in {32, 64, 128} and
+ * CTA shape (4 or 8 warps), and returns the fastest with its throughput in
+ * algorithmic GB/s (Eq. EstimateT bytes).  Builds and frees its own matrices. */
+fd_status fd_tune_batched(fd_ctx* ctx, int n_inst, const char* const* specs, int n_target,
+                          int probe_degree, int* nb, int* C, int* cta_warps, double* gbs);
+
 /* Kernel-polynomial moments mu_m = (1/(R D)) sum_r r^T T_m(A~) r, m <
  * n_moments, with R = n_random normal-like random vectors (SplitMix64 stream
  * 4, `seed`) and A~ = alpha H + beta I (Sec. 4.1 computes the DOS with KPM).
@@ -239,6 +283,39 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b,
 fd_status fd_kpm_moments(fd_ctx* ctx, const fd_matrix* A, int n_moments,
                          int n_random, uint64_t seed, double alpha, double beta,
                          double* mu);
+
+/* ------------------------------------------------------- filter-parameter predictor
+ * A 64-128-128-3 perceptron (FP32 weights, GELU activations) that predicts
+ * the degree constant c_n and the window margins m_l, m_r of fd_solve's
+ * interval heuristic from kernel-polynomial density-of-states moments and the
+ * target window.  The paper has no learned component; the network is trained
+ * on logs of FD runs by the project's own kernels.  Parameters are one FP32
+ * device vector of fd_mlp_num_params() numbers: W1 (64x128 row-major), b1,
+ * W2 (128x128), b2, W3 (128x3), b3. */
+int fd_mlp_num_params(void);
+/* Y (device B x 3) = network(X (device B x 64)). */
+fd_status fd_mlp_forward(fd_ctx* ctx, const float* params, const float* X, int B, float* Y);
+/* Gradient (device, fd_mlp_num_params() floats) of the mean-squared error
+ * between the outputs and T (device B x 3); loss is a HOST float. */
+fd_status fd_mlp_gradient(fd_ctx* ctx, const float* params, const float* X, const float* T,
+                          int B, float* grad, float* loss);
+/* One Adam step (Kingma & Ba; b1 = 0.9, b2 = 0.999, eps = 1e-8, step >= 1 is
+ * the 1-based update count) on the batch; m, v: device moment vectors (start
+ * at zero); loss: optional HOST float (the loss before the update). */
+fd_status fd_mlp_train_step(fd_ctx* ctx, float* params, float* m, float* v, const float* X,
+                            const float* T, int B, int step, float lr, float* loss);
+/* The 64 input features of one problem (HOST floats): the 48 KPM moments of
+ * the matrix scaled by its inclusion interval (16 random vectors of `seed`),
+ * the scaled window ends and width, n_target/100, log10(D)/8, nnz/(32 D), the
+ * interval ends relative to the larger of their magnitudes, log10(1 + KPM
+ * eigenvalue count in [a, b])/6, min(4, count/ns), nb/128, ns/1024, zeros. */
+fd_status fd_filter_features(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_target,
+                             int nb, int ns, uint64_t seed, float* feat);
+/* c_n = exp(y0) in [1, 16], m_l = y1 and m_r = y2 clipped to [0.05, 0.95];
+ * a non-finite output selects the plain heuristic (4, 0.5, 0.5) and sets
+ * *fallback = 1.  feat: HOST 64 floats. */
+fd_status fd_predict_filter_params(fd_ctx* ctx, const float* params, const float* feat,
+                                   double* c_n, double* m_l, double* m_r, int* fallback);
 
 #ifdef __cplusplus
 }

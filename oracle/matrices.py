@@ -179,6 +179,35 @@ def anderson_instance(s):
     return 16 + int(np.floor(33.0 * uL)), 2.0 + 14.0 * uW
 
 
+def roadgraph(side, q=0.3, seed=0):
+    """Road-like planar graph Laplacian L = D_g - A on a side x side grid.
+
+    Node i = x + side*y.  A random spanning tree: every node except (0, 0)
+    keeps one edge to a parent that precedes it -- row 0 links left; column 0
+    links down; elsewhere left if u < 1/2 else down (u from stream 7, counter
+    i).  Every other grid edge (the left and the down edge of node i) is added
+    with probability q (stream 8, counters 2i and 2i+1), so the mean degree is
+    about 2 (1 + q): connected, planar, irregular.
+    """
+    N = side * side
+    i = np.arange(N, dtype=np.int64)
+    x, y = i % side, i // side
+    u_par = splitmix.uniform(seed, splitmix.STREAM_ROAD_TREE, i)
+    par_left = (y == 0) & (x > 0) | (y > 0) & (x > 0) & (u_par < 0.5)
+    par_down = (y > 0) & ((x == 0) | (u_par >= 0.5))
+    u_l = splitmix.uniform(seed, splitmix.STREAM_ROAD_EXTRA, 2 * i)
+    u_d = splitmix.uniform(seed, splitmix.STREAM_ROAD_EXTRA, 2 * i + 1)
+    left = par_left | ((x > 0) & ~par_left & (u_l < q))
+    down = par_down | ((y > 0) & ~par_down & (u_d < q))
+    a = np.concatenate([i[left], i[down]])
+    b = np.concatenate([i[left] - 1, i[down] - side])
+    deg = np.bincount(a, minlength=N) + np.bincount(b, minlength=N)
+    rows = np.concatenate([a, b, i])
+    cols = np.concatenate([b, a, i])
+    vals = np.concatenate([-np.ones(len(a)), -np.ones(len(a)), deg.astype(np.float64)])
+    return _csr_from_coo(N, rows, cols, vals)
+
+
 def chain(n, t=1.0):
     """Open tight-binding chain: -t on the first off-diagonals, 0 diagonal."""
     rows, cols, vals = [np.arange(n)], [np.arange(n)], [np.zeros(n)]
@@ -216,6 +245,8 @@ def build(spec):
                           float(kv.get("t", 1)))
     if kind == "chain":
         return chain(int(kv["n"]), float(kv.get("t", 1)))
+    if kind == "roadgraph":
+        return roadgraph(int(kv["side"]), float(kv.get("q", 0.3)), int(kv.get("seed", 0)))
     raise ValueError(f"unknown matrix kind {kind!r}")
 
 

@@ -19,7 +19,7 @@ converted once, so its value does not depend on the order of additions.
 
 Stream identifiers (fixed constants of this project):
     1 disorder, 2 start block, 3 Lanczos start vector, 4 KPM random vectors,
-    5 instance size L, 6 instance disorder W.
+    5 instance size L, 6 instance disorder W, 7 road-graph tree, 8 road-graph extra edges.
 """
 import numpy as np
 
@@ -33,6 +33,8 @@ STREAM_LANCZOS = 3
 STREAM_KPM = 4
 STREAM_INST_L = 5
 STREAM_INST_W = 6
+STREAM_ROAD_TREE = 7
+STREAM_ROAD_EXTRA = 8
 
 
 def mix64(z):

@@ -42,7 +42,11 @@ class fd_matrix_info(ctypes.Structure):
 class fd_options(ctypes.Structure):
     _fields_ = [("ns", _i32), ("max_outer", _i32), ("n_max", _i32), ("lanczos_steps", _i32),
                 ("seed", ctypes.c_uint64), ("precision", _i32), ("c_n", _dbl), ("m_l", _dbl),
-                ("m_r", _dbl), ("verbose", _i32)]
+                ("m_r", _dbl), ("verbose", _i32), ("cta_warps", _i32)]
+
+
+class fd_problem(ctypes.Structure):
+    _fields_ = [("a", _dbl), ("b", _dbl), ("n_target", _i32), ("seed", ctypes.c_uint64)]
 
 
 class fd_result(ctypes.Structure):
@@ -50,7 +54,7 @@ class fd_result(ctypes.Structure):
                 ("n_spmmv_f32", _i64), ("final_degree", _i32), ("ns", _i32), ("lam_l", _dbl),
                 ("lam_r", _dbl), ("window_l", _dbl), ("window_r", _dbl), ("t_total", _dbl),
                 ("t_bounds", _dbl), ("t_filter", _dbl), ("t_ortho", _dbl), ("t_rr", _dbl),
-                ("filter_bytes", _dbl)]
+                ("filter_bytes", _dbl), ("used_graph", _i32)]
 
 
 _SIGS = {
@@ -74,6 +78,21 @@ _SIGS = {
     "fd_rayleigh_ritz": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, _i64, _pd, _pd]),
     "fd_solve": (_i32, [_vp, _vp, _dbl, _dbl, _i32, _i32, _i32, _dbl, ctypes.POINTER(fd_options),
                         ctypes.POINTER(fd_result), _pd, _pd, _vp, _i64]),
+    "fd_solve_batched": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(fd_problem), _i32,
+                                _i32, _dbl, ctypes.POINTER(fd_options), ctypes.POINTER(fd_result),
+                                _pd, _pd]),
+    "fd_tune_batched": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_char_p), _i32, _i32,
+                               ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                               ctypes.POINTER(_dbl)]),
+    "fd_mlp_num_params": (_i32, []),
+    "fd_mlp_forward": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "fd_mlp_gradient": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, ctypes.POINTER(ctypes.c_float)]),
+    "fd_mlp_train_step": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float,
+                                 ctypes.POINTER(ctypes.c_float)]),
+    "fd_filter_features": (_i32, [_vp, _vp, _dbl, _dbl, _i32, _i32, _i32, ctypes.c_uint64,
+                                  ctypes.POINTER(ctypes.c_float)]),
+    "fd_predict_filter_params": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_float), _pd, _pd, _pd,
+                                        ctypes.POINTER(_i32)]),
     "fd_kpm_moments": (_i32, [_vp, _vp, _i32, _i32, ctypes.c_uint64, _dbl, _dbl, _pd]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -293,8 +312,95 @@ def fd_solve(ctx, A, a, b, n_target, nb, degree, tol, X=None, raise_noconv=True,
     return theta, resid, {k: getattr(res, k) for k, _ in fd_result._fields_}
 
 
+def fd_solve_batched(ctx, mats, problems, nb, degree, tol, raise_noconv=True, **opts):
+    """problems: list of (a, b, n_target, seed).  Returns (list of (theta, resid),
+    list of result dicts)."""
+    n = len(mats)
+    arr = (_vp * n)(*[m.handle for m in mats])
+    pr = (fd_problem * n)(*[fd_problem(a, b, nt, sd) for (a, b, nt, sd) in problems])
+    o = fd_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    res = (fd_result * n)()
+    tot = sum(p[2] for p in problems)
+    theta = np.empty(tot)
+    resid = np.empty(tot)
+    st = _lib.fd_solve_batched(ctx.handle, n, arr, pr, nb, degree, tol, ctypes.byref(o), res,
+                               _dptr(theta, ctypes.c_double), _dptr(resid, ctypes.c_double))
+    if st != FD_OK and not (st == FD_ERR_NOCONV and not raise_noconv):
+        _check(ctx, st)
+    out, o_ = [], 0
+    for p in problems:
+        out.append((theta[o_:o_ + p[2]].copy(), resid[o_:o_ + p[2]].copy()))
+        o_ += p[2]
+    return out, [{k: getattr(r, k) for k, _ in fd_result._fields_} for r in res]
+
+
+def fd_tune_batched(ctx, specs, n_target, probe_degree=20):
+    n = len(specs)
+    arr = (ctypes.c_char_p * n)(*[s.encode() for s in specs])
+    nb, C, w, g = _i32(), _i32(), _i32(), _dbl()
+    _check(ctx, _lib.fd_tune_batched(ctx.handle, n, arr, n_target, probe_degree, ctypes.byref(nb),
+                                     ctypes.byref(C), ctypes.byref(w), ctypes.byref(g)))
+    return {"nb": nb.value, "C": C.value, "cta_warps": w.value, "gbs": g.value}
+
+
 def fd_kpm_moments(ctx, A, n_moments, n_random, seed, alpha, beta):
     mu = np.empty(n_moments)
     _check(ctx, _lib.fd_kpm_moments(ctx.handle, A.handle, n_moments, n_random, seed, alpha, beta,
                                     _dptr(mu, ctypes.c_double)))
     return mu
+
+
+# ---------------------------------------------------------------- predictor
+def fd_mlp_num_params():
+    return _lib.fd_mlp_num_params()
+
+
+def _f32(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor")
+    return _vp(t.data_ptr())
+
+
+def fd_mlp_forward(ctx, params, X):
+    import torch
+    Y = torch.empty((X.shape[0], 3), dtype=torch.float32, device=X.device)
+    _check(ctx, _lib.fd_mlp_forward(ctx.handle, _f32(params, "params"), _f32(X, "X"), X.shape[0],
+                                    _f32(Y, "Y")))
+    return Y
+
+
+def fd_mlp_gradient(ctx, params, X, T):
+    import torch
+    g = torch.empty_like(params)
+    loss = ctypes.c_float()
+    _check(ctx, _lib.fd_mlp_gradient(ctx.handle, _f32(params, "params"), _f32(X, "X"), _f32(T, "T"),
+                                     X.shape[0], _f32(g, "grad"), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def fd_mlp_train_step(ctx, params, m, v, X, T, step, lr):
+    loss = ctypes.c_float()
+    _check(ctx, _lib.fd_mlp_train_step(ctx.handle, _f32(params, "params"), _f32(m, "m"), _f32(v, "v"),
+                                       _f32(X, "X"), _f32(T, "T"), X.shape[0], step, lr,
+                                       ctypes.byref(loss)))
+    return loss.value
+
+
+def fd_filter_features(ctx, A, a, b, n_target, nb, ns, seed=0):
+    f = np.zeros(64, dtype=np.float32)
+    _check(ctx, _lib.fd_filter_features(ctx.handle, A.handle, a, b, n_target, nb, ns, seed,
+                                        f.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return f
+
+
+def fd_predict_filter_params(ctx, params, feat):
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    c, ml, mr, fb = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), _i32()
+    _check(ctx, _lib.fd_predict_filter_params(ctx.handle, _f32(params, "params"),
+                                              feat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              ctypes.byref(c), ctypes.byref(ml), ctypes.byref(mr),
+                                              ctypes.byref(fb)))
+    return {"c_n": c.value, "m_l": ml.value, "m_r": mr.value, "fallback": fb.value}

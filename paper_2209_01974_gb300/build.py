@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfd.so")
-SOURCES = ["fd_matrix.cu", "fd_filter.cu", "fd_dense.cu", "fd_solve.cu"]
+SOURCES = ["fd_matrix.cu", "fd_filter.cu", "fd_dense.cu", "fd_solve.cu", "fd_batched.cu", "fd_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
          "--expt-relaxed-constexpr"]
@@ -36,8 +36,8 @@ def _stale(obj, deps):
 def build(verbose=False, force=False):
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "fd_internal.cuh"),
-               os.path.join(os.path.dirname(HERE), "include", "fd.h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
+    headers.append(os.path.join(os.path.dirname(HERE), "include", "fd.h"))
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
 
     def compile_one(src):

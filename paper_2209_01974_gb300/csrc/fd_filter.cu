@@ -18,188 +18,21 @@
 #include <vector>
 
 #include "fd_internal.cuh"
+#include "fd_step.cuh"
 
 namespace fdi {
 namespace {
 
-template <typename T>
-struct V16;
-template <>
-struct V16<double> {
-  static constexpr int E = 2;
-  double v[2];
-  __device__ __forceinline__ void ldg(const double* p) {
-    double2 t = __ldg(reinterpret_cast<const double2*>(p));
-    v[0] = t.x; v[1] = t.y;
-  }
-  __device__ __forceinline__ void ldcs(const double* p) {
-    double2 t = __ldcs(reinterpret_cast<const double2*>(p));
-    v[0] = t.x; v[1] = t.y;
-  }
-  __device__ __forceinline__ void stcs(double* p) const {
-    __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
-  }
-  __device__ __forceinline__ void st(double* p) const {
-    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-  }
-};
-template <>
-struct V16<float> {
-  static constexpr int E = 4;
-  float v[4];
-  __device__ __forceinline__ void ldg(const float* p) {
-    float4 t = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-  }
-  __device__ __forceinline__ void ldcs(const float* p) {
-    float4 t = __ldcs(reinterpret_cast<const float4*>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-  }
-  __device__ __forceinline__ void stcs(float* p) const {
-    __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
-  }
-  __device__ __forceinline__ void st(float* p) const {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  }
-};
-
-template <typename T>
-struct SellArgs {
-  const int64_t* chunk_ptr;
-  const int32_t* row_len;
-  const int32_t* col;
-  const T* val;
-  int64_t D;
-  int C;
-};
-
-enum { MODE_SPMMV = 0, MODE_SECOND = 1, MODE_GENERIC = 2 };
-
-template <typename T>
-struct StepArgs {
-  const T* X; int64_t ldx;   // gathered operand x_{k-1}
-  const T* Z; int64_t ldz;   // x_{k-2}, row-wise (may alias Y or Vout at the same row)
-  T* Y; int64_t ldy;         // x_k output, or nullptr
-  const T* Vin; int64_t ldvi;
-  T* Vout; int64_t ldvo;
-  T c_ax, c_x;               // x_k = c_ax * (A x_{k-1}) + c_x * x_{k-1} [- x_{k-2}]
-  T mu0, mu1, mu2;           // SECOND: Vout = mu0 z + mu1 x + mu2 y; GENERIC: Vout = Vin + mu2 y
-};
-
-constexpr int WARPS = 8;
-constexpr int UNROLL = 4;
-
-template <typename T, int NB>
-struct Layout {
-  static constexpr int E = V16<T>::E;
-  static constexpr int Q = NB / E;                 // 16-byte vectors per row
-  static constexpr int G = Q >= 32 ? 32 : Q;        // lanes per row
-  static constexpr int CPL = Q / G;                 // vectors per lane
-  static constexpr int RPW = 32 / G;                // rows per warp
-  static_assert(NB % E == 0 && Q % G == 0, "nb must fill whole 16-byte vectors");
-};
-
-// Gather-accumulate s = sum_j a_ij x_j over the SELL row, returning the row's
-// own vector xi (entry 0 is the diagonal).
-template <typename T, int NB>
-__device__ __forceinline__ void row_product(const SellArgs<T>& A, const T* __restrict__ X,
-                                            int64_t ldx, int64_t row, bool active, int wlen,
-                                            int gl, V16<T> (&acc)[Layout<T, NB>::CPL],
-                                            V16<T> (&xi)[Layout<T, NB>::CPL]) {
-  using L = Layout<T, NB>;
-  constexpr int E = L::E;
-  // Rows at or beyond D inside the last chunk are SELL padding rows: their
-  // entries exist (value 0, column 0), but they have no vector row.
-  const int64_t base = A.chunk_ptr[row / A.C] + (row % A.C);
-  const int64_t rx = active ? row : 0;
-  const T* xl = X + gl * E;
-  const T a0 = active ? A.val[base] : T(0);
-#pragma unroll
-  for (int v = 0; v < L::CPL; ++v) {
-    xi[v].ldg(xl + rx * ldx + v * L::G * E);
-#pragma unroll
-    for (int e = 0; e < E; ++e) acc[v].v[e] = a0 * xi[v].v[e];
-  }
-  int j = 1;
-  for (; j + UNROLL <= wlen; j += UNROLL) {
-    int32_t c[UNROLL];
-    T a[UNROLL];
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u) {
-      c[u] = __ldg(A.col + base + (int64_t)(j + u) * A.C);
-      a[u] = __ldg(A.val + base + (int64_t)(j + u) * A.C);
-    }
-    V16<T> x[UNROLL][L::CPL];
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u)
-#pragma unroll
-      for (int v = 0; v < L::CPL; ++v) x[u][v].ldg(xl + (int64_t)c[u] * ldx + v * L::G * E);
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u)
-#pragma unroll
-      for (int v = 0; v < L::CPL; ++v)
-#pragma unroll
-        for (int e = 0; e < E; ++e) acc[v].v[e] = fma(a[u], x[u][v].v[e], acc[v].v[e]);
-  }
-  for (; j < wlen; ++j) {
-    int32_t c = __ldg(A.col + base + (int64_t)j * A.C);
-    T a = __ldg(A.val + base + (int64_t)j * A.C);
-#pragma unroll
-    for (int v = 0; v < L::CPL; ++v) {
-      V16<T> x;
-      x.ldg(xl + (int64_t)c * ldx + v * L::G * E);
-#pragma unroll
-      for (int e = 0; e < E; ++e) acc[v].v[e] = fma(a, x.v[e], acc[v].v[e]);
-    }
-  }
-}
+using namespace step;
 
 template <typename T, int NB, int MODE>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, MIN_BLOCKS)
     k_cheb_step(SellArgs<T> A, StepArgs<T> s) {
   using L = Layout<T, NB>;
-  constexpr int E = L::E;
-  const int lane = threadIdx.x & 31;
-  const int g = lane / L::G, gl = lane % L::G;
   const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
   const int64_t row0 = warp * L::RPW;
   if (row0 >= A.D) return;
-  const int64_t row = row0 + g;
-  const bool active = row < A.D;
-  const int len = active ? A.row_len[row] : 0;
-  const int wlen = __reduce_max_sync(0xffffffffu, len);
-
-  V16<T> acc[L::CPL], xi[L::CPL];
-  row_product<T, NB>(A, s.X, s.ldx, row, active, wlen, gl, acc, xi);
-  if (!active) return;
-
-#pragma unroll
-  for (int v = 0; v < L::CPL; ++v) {
-    const int64_t off = gl * E + v * L::G * E;
-    V16<T> y;
-    if (MODE == MODE_SPMMV) {
-#pragma unroll
-      for (int e = 0; e < E; ++e) y.v[e] = s.c_ax * acc[v].v[e] + s.c_x * xi[v].v[e];
-      y.st(s.Y + row * s.ldy + off);
-    } else {
-      V16<T> z, o;
-      z.ldcs(s.Z + row * s.ldz + off);
-#pragma unroll
-      for (int e = 0; e < E; ++e) y.v[e] = s.c_ax * acc[v].v[e] + s.c_x * xi[v].v[e] - z.v[e];
-      if (MODE == MODE_SECOND) {
-#pragma unroll
-        for (int e = 0; e < E; ++e)
-          o.v[e] = s.mu0 * z.v[e] + s.mu1 * xi[v].v[e] + s.mu2 * y.v[e];
-      } else {
-        V16<T> vin;
-        vin.ldcs(s.Vin + row * s.ldvi + off);
-#pragma unroll
-        for (int e = 0; e < E; ++e) o.v[e] = vin.v[e] + s.mu2 * y.v[e];
-      }
-      if (s.Y) y.st(s.Y + row * s.ldy + off);
-      o.stcs(s.Vout + row * s.ldvo + off);
-    }
-  }
+  cheb_rows<T, NB, MODE>(A, s, row0);
 }
 
 // dst[i] = src[perm[i]] (to SELL order) or dst[perm[i]] = src[i] (back)
@@ -365,7 +198,7 @@ __global__ void k_kpm_init(double* r, int64_t D, int R, const int64_t* perm, uin
 // one step: x_new = c_ax * A x + c_x * x [- z]; partial[blk] = (sum x_new . x, sum x_new . x_new,
 // sum x . x); grid-stride over rows so the number of partials is fixed
 template <int NB, bool FIRST>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, MIN_BLOCKS)
     k_kpm_step(SellArgs<double> A, const double* X, const double* Z, double* Y, double c_ax,
                double c_x, double* partial) {
   using L = Layout<double, NB>;
@@ -381,7 +214,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     const int len = active ? A.row_len[row] : 0;
     const int wlen = __reduce_max_sync(0xffffffffu, len);
     V16<double> acc[L::CPL], xi[L::CPL];
-    row_product<double, NB>(A, X, NB, row, active, wlen, gl, acc, xi);
+    row_product<double, NB>(A, X, NB, row, active, len, wlen, gl, acc, xi);
     if (active) {
 #pragma unroll
       for (int v = 0; v < L::CPL; ++v) {

@@ -27,7 +27,8 @@ struct fd_ctx {
 };
 
 struct fd_matrix {
-  fd_ctx* ctx = nullptr;
+  fd_ctx* ctx = nullptr;  // creating context (not dereferenced by fd_matrix_free)
+  int device = 0;
   int64_t D = 0, nnz = 0, nnz_sell = 0, n_chunks = 0;
   int C = 32, sigma = 1, max_row = 0, identity = 1;
   double gersh_lo = 0, gersh_hi = 0;
@@ -140,6 +141,7 @@ std::vector<double> filter_coeffs(double x_l, double x_r, int n);
 namespace fdrng {
 constexpr uint64_t GAMMA = 0x9E3779B97F4A7C15ull;
 constexpr int STREAM_DISORDER = 1, STREAM_START = 2, STREAM_LANCZOS = 3, STREAM_KPM = 4;
+constexpr int STREAM_ROAD_TREE = 7, STREAM_ROAD_EXTRA = 8;
 __host__ __device__ inline uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

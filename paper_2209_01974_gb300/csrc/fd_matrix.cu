@@ -289,6 +289,57 @@ __global__ void k_anderson_fill(AndersonP p, int64_t* rowptr, int32_t* col, doub
   if (r == p.D - 1) rowptr[p.D] = 7 * p.D;
 }
 
+// road-like planar graph (see fd_build_matrix): edges of node i to its left
+// and lower neighbours; the right and upper edges belong to those neighbours
+struct RoadP {
+  int64_t side, N;
+  double q;
+  uint64_t ktree, kextra;
+};
+
+__device__ inline void road_own_edges(const RoadP& p, int64_t i, bool* left, bool* down) {
+  const int64_t x = i % p.side, y = i / p.side;
+  const double u = fdrng::uniform(p.ktree, (uint64_t)i);
+  const bool pl = (y == 0 && x > 0) || (y > 0 && x > 0 && u < 0.5);
+  const bool pd = y > 0 && (x == 0 || u >= 0.5);
+  *left = pl || (x > 0 && !pl && fdrng::uniform(p.kextra, (uint64_t)(2 * i)) < p.q);
+  *down = pd || (y > 0 && !pd && fdrng::uniform(p.kextra, (uint64_t)(2 * i + 1)) < p.q);
+}
+
+// neighbours of node i in ascending order: down, left, (self), right, up
+__device__ inline int road_neighbours(const RoadP& p, int64_t i, int64_t* nb) {
+  bool l, d, rl = false, ud = false, dummy;
+  road_own_edges(p, i, &l, &d);
+  const int64_t x = i % p.side, y = i / p.side;
+  if (x + 1 < p.side) road_own_edges(p, i + 1, &rl, &dummy);
+  if (y + 1 < p.side) road_own_edges(p, i + p.side, &dummy, &ud);
+  int n = 0;
+  if (d) nb[n++] = i - p.side;
+  if (l) nb[n++] = i - 1;
+  if (rl) nb[n++] = i + 1;
+  if (ud) nb[n++] = i + p.side;
+  return n;
+}
+
+__global__ void k_road_count(RoadP p, int64_t* cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.N) return;
+  int64_t nb[4];
+  cnt[i] = 1 + road_neighbours(p, i, nb);
+}
+
+__global__ void k_road_fill(RoadP p, const int64_t* rowptr, int32_t* col, double* val) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.N) return;
+  int64_t nb[4];
+  const int n = road_neighbours(p, i, nb);
+  int64_t o = rowptr[i];
+  int k = 0;
+  for (; k < n && nb[k] < i; ++k) { col[o] = (int32_t)nb[k]; val[o] = -1.0; ++o; }
+  col[o] = (int32_t)i; val[o] = (double)n; ++o;
+  for (; k < n; ++k) { col[o] = (int32_t)nb[k]; val[o] = -1.0; ++o; }
+}
+
 __global__ void k_chain_fill(int64_t n, double t, int64_t* rowptr, int32_t* col, double* val) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -368,6 +419,9 @@ __global__ void k_chunk_len(const int32_t* len, const int64_t* perm, const uint8
     row_len[i] = l;
     m = max(m, l);
   }
+  // chunk length rounded up to a multiple of 8 entries: the SpMMV kernels take
+  // entries in batches of 8 without per-entry predicates
+  m = (m + 7) & ~7;
   chunk_sz[c] = (int64_t)m * C;
 }
 
@@ -692,6 +746,7 @@ fd_status fd_build_matrix_sell(fd_ctx* ctx, const char* spec, int C, int sigma,
   cudaStream_t st = ctx->stream;
   fd_matrix* A = new fd_matrix();
   A->ctx = ctx;
+  A->device = ctx->device;
   A->C = C;
   A->sigma = sigma;
   int64_t* rowptr = nullptr;
@@ -751,6 +806,32 @@ fd_status fd_build_matrix_sell(fd_ctx* ctx, const char* spec, int C, int sigma,
     FD_CUDA(ctx, cudaMalloc(&val, sizeof(double) * nnz));
     k_anderson_fill<<<(unsigned)cdiv(p.D, T), T, 0, st>>>(p, rowptr, col, val);
     FD_LAUNCHED(ctx);
+  } else if (s.kind == "roadgraph") {
+    long long side, seed;
+    double q;
+    if (!get_int(s, "side", &side, true, 0) || !get_int(s, "seed", &seed, false, 0) ||
+        !get_dbl(s, "q", &q, 0.3) || side < 2 || side > 46340 || !(q >= 0.0 && q <= 1.0)) {
+      delete A;
+      return set_err(ctx, FD_ERR_ARG, "roadgraph needs integer 2 <= side <= 46340, 0 <= q <= 1, integer seed");
+    }
+    RoadP p;
+    p.side = side; p.N = side * side; p.q = q;
+    p.ktree = fdrng::key((uint64_t)seed, fdrng::STREAM_ROAD_TREE);
+    p.kextra = fdrng::key((uint64_t)seed, fdrng::STREAM_ROAD_EXTRA);
+    A->D = p.N;
+    int64_t* cnt;
+    FD_CUDA(ctx, cudaMalloc(&rowptr, sizeof(int64_t) * (p.N + 1)));
+    FD_CUDA(ctx, cudaMalloc(&cnt, sizeof(int64_t) * p.N));
+    k_road_count<<<(unsigned)cdiv(p.N, T), T, 0, st>>>(p, cnt);
+    FD_LAUNCHED(ctx);
+    FD_TRY(exclusive_scan(ctx, cnt, p.N, rowptr));
+    FD_CUDA(ctx, cudaMemcpyAsync(&nnz, rowptr + p.N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    FD_CUDA(ctx, cudaStreamSynchronize(st));
+    cudaFree(cnt);
+    FD_CUDA(ctx, cudaMalloc(&col, sizeof(int32_t) * nnz));
+    FD_CUDA(ctx, cudaMalloc(&val, sizeof(double) * nnz));
+    k_road_fill<<<(unsigned)cdiv(p.N, T), T, 0, st>>>(p, rowptr, col, val);
+    FD_LAUNCHED(ctx);
   } else if (s.kind == "chain") {
     long long n;
     double t;
@@ -795,7 +876,7 @@ fd_status fd_matrix_from_csr(fd_ctx* ctx, int64_t D, const int64_t* rowptr, cons
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
   int64_t nnz = rowptr[D];
   fd_matrix* A = new fd_matrix();
-  A->ctx = ctx; A->D = D; A->C = C; A->sigma = sigma;
+  A->ctx = ctx; A->device = ctx->device; A->D = D; A->C = C; A->sigma = sigma;
   int64_t* d_rowptr;
   int32_t* d_col;
   double* d_val;
@@ -812,10 +893,9 @@ fd_status fd_matrix_from_csr(fd_ctx* ctx, int64_t D, const int64_t* rowptr, cons
 
 fd_status fd_matrix_free(fd_matrix* A) {
   if (!A) return FD_ERR_ARG;
-  if (A->ctx) {
-    cudaSetDevice(A->ctx->device);
-    cudaStreamSynchronize(A->ctx->stream);
-  }
+  // the context may already be gone: use the device recorded at creation
+  cudaSetDevice(A->device);
+  cudaDeviceSynchronize();
   cudaFree(A->chunk_ptr); cudaFree(A->row_len); cudaFree(A->col); cudaFree(A->val);
   cudaFree(A->val32); cudaFree(A->perm); cudaFree(A->iperm); cudaFree(A->diag_added);
   delete A;

@@ -1,0 +1,227 @@
+// Device building blocks of the fused Chebyshev step (Sec. 2, Alg. 2), shared
+// by the single-block filter and the batched persistent filter.
+//
+// Work mapping: a group of G lanes owns one SELL row; each lane holds CPL
+// 16-byte vectors of the row (G * CPL * 16 bytes = nb * sizeof(T)), so every
+// gathered row of W1 is one fully coalesced access.  A warp holds 32/G
+// consecutive rows of one SELL chunk, so the warp's matrix loads at entry j
+// touch adjacent words of the chunk's column-major slab.  Entry 0 of every
+// SELL row is its diagonal, so the row's own W1 vector (needed for the beta
+// term) is the first gathered vector.  W2 and V are touched once per step and
+// use evict-first (.cs) loads and stores, keeping L2 for the W1 gathers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdi {
+namespace step {
+
+template <typename T>
+struct V16;
+template <>
+struct V16<double> {
+  static constexpr int E = 2;
+  double v[2];
+  __device__ __forceinline__ void ldg(const double* p) {
+    double2 t = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = t.x; v[1] = t.y;
+  }
+  __device__ __forceinline__ void ldcs(const double* p) {
+    double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+    v[0] = t.x; v[1] = t.y;
+  }
+  __device__ __forceinline__ void stcs(double* p) const {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+  }
+  __device__ __forceinline__ void st(double* p) const {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+template <>
+struct V16<float> {
+  static constexpr int E = 4;
+  float v[4];
+  __device__ __forceinline__ void ldg(const float* p) {
+    float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ __forceinline__ void ldcs(const float* p) {
+    float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ __forceinline__ void stcs(float* p) const {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  }
+  __device__ __forceinline__ void st(float* p) const {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+template <typename T>
+struct SellArgs {
+  const int64_t* chunk_ptr;
+  const int32_t* row_len;
+  const int32_t* col;
+  const T* val;
+  int64_t D;
+  int C;
+};
+
+enum { MODE_SPMMV = 0, MODE_SECOND = 1, MODE_GENERIC = 2 };
+
+template <typename T>
+struct StepArgs {
+  const T* X; int64_t ldx;   // gathered operand x_{k-1}
+  const T* Z; int64_t ldz;   // x_{k-2}, row-wise (may alias Y or Vout at the same row)
+  T* Y; int64_t ldy;         // x_k output, or nullptr
+  const T* Vin; int64_t ldvi;
+  T* Vout; int64_t ldvo;
+  T c_ax, c_x;               // x_k = c_ax * (A x_{k-1}) + c_x * x_{k-1} [- x_{k-2}]
+  T mu0, mu1, mu2;           // SECOND: Vout = mu0 z + mu1 x + mu2 y; GENERIC: Vout = Vin + mu2 y
+};
+
+constexpr int WARPS = 8;
+constexpr int BATCH = 8;   // entries per batch; SELL chunk lengths are multiples of 8
+constexpr int MIN_BLOCKS = 4;  // >= 32 resident warps per SM (<= 64 registers)
+
+template <typename T, int NB>
+struct Layout {
+  static constexpr int E = V16<T>::E;
+  static constexpr int Q = NB / E;                 // 16-byte vectors per row
+  static constexpr int G = Q >= 32 ? 32 : Q;        // lanes per row
+  static constexpr int CPL = Q / G;                 // vectors per lane
+  static constexpr int RPW = 32 / G;                // rows per warp
+  static_assert(NB % E == 0 && Q % G == 0, "nb must fill whole 16-byte vectors");
+};
+
+// Gather-accumulate s = sum_j a_ij x_j over the SELL row, returning the row's
+// own vector xi (entry 0 is the diagonal).  Entries are taken BATCH at a time:
+// the matrix loads of a batch, then all its gathers, so a row of up to BATCH
+// entries costs one round trip of dependent loads.  Chunk lengths are padded to
+// a multiple of BATCH with (0, own row) entries, so the matrix loads need no
+// bounds; the gathers and FMAs of entries past the row's own length are
+// skipped (FP64 arithmetic, not memory, bounds the FP64 step on GB300).
+template <typename T, int NB>
+__device__ __forceinline__ void row_product(const SellArgs<T>& A, const T* __restrict__ X,
+                                            int64_t ldx, int64_t row, bool active, int len,
+                                            int wlen, int gl, V16<T> (&acc)[Layout<T, NB>::CPL],
+                                            V16<T> (&xi)[Layout<T, NB>::CPL]) {
+  using L = Layout<T, NB>;
+  constexpr int E = L::E;
+  // Rows at or beyond D inside the last chunk are SELL padding rows: their
+  // entries exist (value 0, column 0), but they have no vector row.
+  const int64_t base = A.chunk_ptr[row / A.C] + (row % A.C);
+  const int32_t* cp = A.col + base;
+  const T* vp = A.val + base;
+  const uint32_t C = (uint32_t)A.C;
+  const uint32_t ld = (uint32_t)ldx;
+  const T* xl = X + gl * E;
+  {
+    int32_t c[BATCH];
+    T a[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      c[u] = __ldg(cp + u * C);
+      a[u] = __ldg(vp + u * C);
+    }
+    if (!active) { c[0] = 0; a[0] = T(0); }
+#pragma unroll
+    for (int v = 0; v < L::CPL; ++v) {
+      xi[v].ldg(xl + (uint64_t)(uint32_t)c[0] * ld + v * L::G * E);
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[v].v[e] = a[0] * xi[v].v[e];
+    }
+#pragma unroll
+    for (int u = 1; u < BATCH; ++u) {
+      if (u < len) {  // entries past the row's length are padding: skip their FMAs
+#pragma unroll
+        for (int v = 0; v < L::CPL; ++v) {
+          V16<T> x;
+          x.ldg(xl + (uint64_t)(uint32_t)c[u] * ld + v * L::G * E);
+#pragma unroll
+          for (int e = 0; e < E; ++e) acc[v].v[e] = fma(a[u], x.v[e], acc[v].v[e]);
+        }
+      }
+    }
+  }
+  for (int j0 = BATCH; j0 < wlen; j0 += BATCH) {
+    int32_t c[BATCH];
+    T a[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      c[u] = __ldg(cp + (j0 + u) * C);
+      a[u] = __ldg(vp + (j0 + u) * C);
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      if (j0 + u < len) {
+#pragma unroll
+        for (int v = 0; v < L::CPL; ++v) {
+          V16<T> x;
+          x.ldg(xl + (uint64_t)(uint32_t)c[u] * ld + v * L::G * E);
+#pragma unroll
+          for (int e = 0; e < E; ++e) acc[v].v[e] = fma(a[u], x.v[e], acc[v].v[e]);
+        }
+      }
+    }
+  }
+}
+
+// One fused Chebyshev step (or a plain SpMMV) for the warp's rows row0 ..
+// row0 + RPW - 1 (row0 < D, a multiple of RPW); all 32 lanes must call it.
+template <typename T, int NB, int MODE>
+__device__ __forceinline__ void cheb_rows(const SellArgs<T>& A, const StepArgs<T>& s,
+                                          int64_t row0) {
+  using L = Layout<T, NB>;
+  constexpr int E = L::E;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / L::G, gl = lane % L::G;
+  const int64_t row = row0 + g;
+  const bool active = row < A.D;
+  const int len = active ? A.row_len[row] : 0;
+  const int wlen = __reduce_max_sync(0xffffffffu, len);
+
+  // the row-wise operands do not depend on the gathers: issue them first
+  V16<T> z[L::CPL], vin[L::CPL];
+  if (MODE != MODE_SPMMV && active) {
+#pragma unroll
+    for (int v = 0; v < L::CPL; ++v) {
+      const int64_t off = gl * E + v * L::G * E;
+      z[v].ldcs(s.Z + row * s.ldz + off);
+      if (MODE == MODE_GENERIC) vin[v].ldcs(s.Vin + row * s.ldvi + off);
+    }
+  }
+  V16<T> acc[L::CPL], xi[L::CPL];
+  row_product<T, NB>(A, s.X, s.ldx, row, active, len, wlen, gl, acc, xi);
+  if (!active) return;
+
+#pragma unroll
+  for (int v = 0; v < L::CPL; ++v) {
+    const int64_t off = gl * E + v * L::G * E;
+    V16<T> y;
+    if (MODE == MODE_SPMMV) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) y.v[e] = s.c_ax * acc[v].v[e] + s.c_x * xi[v].v[e];
+      y.st(s.Y + row * s.ldy + off);
+    } else {
+      V16<T> o;
+#pragma unroll
+      for (int e = 0; e < E; ++e) y.v[e] = s.c_ax * acc[v].v[e] + s.c_x * xi[v].v[e] - z[v].v[e];
+      if (MODE == MODE_SECOND) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          o.v[e] = s.mu0 * z[v].v[e] + s.mu1 * xi[v].v[e] + s.mu2 * y.v[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) o.v[e] = vin[v].v[e] + s.mu2 * y.v[e];
+      }
+      if (s.Y) y.st(s.Y + row * s.ldy + off);
+      o.stcs(s.Vout + row * s.ldvo + off);
+    }
+  }
+}
+
+
+}  // namespace step
+}  // namespace fdi

@@ -56,7 +56,7 @@ def _params(csr, n, seed=0):
 CASES = [
     ("hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open", 32, 1),
     ("anderson3d:L=11,W=3,seed=5", 64, 1),                 # D = 1331: ragged last chunk
-    ("chain:n=777,t=1", 16, 1),
+    ("chain:n=777,t=1", 64, 8),                             # sigma > 1: permuted rows
 ]
 
 

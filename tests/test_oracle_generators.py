@@ -150,3 +150,26 @@ def test_anderson_instances_in_range():
     Ls, Ws = zip(*[mat.anderson_instance(s) for s in range(64)])
     assert min(Ls) >= 16 and max(Ls) <= 48 and min(Ws) >= 2 and max(Ws) <= 16
     assert len(set(Ls)) > 10
+
+
+def test_roadgraph_is_a_connected_planar_laplacian():
+    import scipy.sparse.csgraph as csg
+    side, q = 40, 0.3
+    rp, c, v = mat.roadgraph(side, q, 5)
+    N = side * side
+    A = mat.to_scipy((rp, c, v))
+    assert abs(A - A.T).max() == 0.0
+    assert np.abs(np.asarray(A.sum(axis=1))).max() == 0.0          # Laplacian rows sum to zero
+    off = A.copy(); off.setdiag(0); off.eliminate_zeros()
+    i, j = off.nonzero()
+    d = np.abs(i - j)
+    assert np.all((d == 1) | (d == side))                           # grid edges only
+    assert np.all((d != 1) | (np.minimum(i, j) % side != side - 1))  # no wrap-around
+    assert csg.connected_components(off)[0] == 1
+    n_edges = off.nnz // 2
+    tree_extra = n_edges - (N - 1)
+    other = 2 * side * (side - 1) - (N - 1)
+    assert abs(tree_extra / other - q) < 0.05                        # extra edges with probability q
+    ev = np.linalg.eigvalsh(A.toarray())
+    assert abs(ev[0]) < 1e-10 and ev[1] > 1e-6                       # one zero mode: connected
+    assert ev[-1] <= 8.0 + 1e-12                                     # Gershgorin: 2 * max degree
