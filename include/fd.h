@@ -186,6 +186,23 @@ fd_status fd_spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec,
 fd_status fd_orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns,
                             int64_t ldv, double* R, int* passes);
 
+/* fd_orthonormalize without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * call cudaMalloc, such as applications whose GPU memory is owned by another
+ * allocator (a framework's caching allocator that has reserved the device) or
+ * serving processes that size their memory once at start-up.  It computes
+ * the same Cholesky-QR as fd_orthonormalize (same arguments, same results
+ * within rounding) but keeps all scratch in a 32 MiB file-scope device array
+ * that every GPU loading the library holds until the process exits.
+ *   ns      at most 256 (larger blocks return FD_ERR_ARG)
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array: calls that overlap on the GPU
+ * (other host threads, other streams) race and must be serialised by the
+ * caller.  It never calls cudaMalloc or cudaFree. */
+fd_status fd_orthonormalize_noalloc(fd_ctx* ctx, double* V, int64_t D, int ns,
+                                    int64_t ldv, double* R, int* passes);
+
 /* Rayleigh-Ritz step (Sec. 2): for an orthonormal D x ns FP64 block V,
  * AV <- H V, Hs = V^T AV, Hs = Q diag(theta) Q^T (theta ascending, FP64
  * Jacobi on the device), V <- V Q, AV <- AV Q and resid_i = ||AV_i -

@@ -75,6 +75,7 @@ _SIGS = {
     "fd_filter_coeffs": (_i32, [_dbl, _dbl, _i32, _pd]),
     "fd_spmmv": (_i32, [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _i32]),
     "fd_orthonormalize": (_i32, [_vp, _vp, _i64, _i32, _i64, _vp, ctypes.POINTER(_i32)]),
+    "fd_orthonormalize_noalloc": (_i32, [_vp, _vp, _i64, _i32, _i64, _vp, ctypes.POINTER(_i32)]),
     "fd_rayleigh_ritz": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, _i64, _pd, _pd]),
     "fd_solve": (_i32, [_vp, _vp, _dbl, _dbl, _i32, _i32, _i32, _dbl, ctypes.POINTER(fd_options),
                         ctypes.POINTER(fd_result), _pd, _pd, _vp, _i64]),
@@ -275,6 +276,19 @@ def fd_orthonormalize(ctx, V, R=None):
     _check(ctx, _lib.fd_orthonormalize(ctx.handle, _vp(pv), D, ns, ldv,
                                        _vp(R.data_ptr() if R is not None else None),
                                        ctypes.byref(passes)))
+    return passes.value
+
+
+def fd_orthonormalize_noalloc(ctx, V, R=None):
+    """fd_orthonormalize for callers that cannot let the library allocate device
+    memory: scratch lives in the library's fixed 32 MiB device array (ns <= 256)."""
+    pv, ldv, D, ns, prec = _block(V, "V")
+    if prec != FD_F64:
+        raise ValueError("fd_orthonormalize_noalloc works on float64 blocks")
+    passes = ctypes.c_int()
+    _check(ctx, _lib.fd_orthonormalize_noalloc(ctx.handle, _vp(pv), D, ns, ldv,
+                                               _vp(R.data_ptr() if R is not None else None),
+                                               ctypes.byref(passes)))
     return passes.value
 
 

@@ -409,6 +409,37 @@ fd_status gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, int64
   return FD_OK;
 }
 
+fd_status gram_partials(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                        int64_t D, int m, int n, double* C, int ldc, bool sym, double* P,
+                        int64_t max_slices) {
+  const int nti = (int)cdiv(m, GT), ntj = (int)cdiv(n, GT);
+  const int tiles = sym ? nti * (nti + 1) / 2 : nti * ntj;
+  int64_t slices = std::max<int64_t>(1, cdiv(4LL * ctx->num_sms, tiles));
+  slices = std::min<int64_t>(slices, std::max<int64_t>(1, cdiv(D, 4 * GK)));
+  slices = std::max<int64_t>(1, std::min<int64_t>(slices, max_slices));
+  const int64_t rps = cdiv(cdiv(D, slices), GK) * GK;
+  slices = std::max<int64_t>(1, cdiv(D, rps));
+  dim3 grid(tiles, (unsigned)slices);
+  k_gram_partial<<<grid, 256, 0, ctx->stream>>>(X, ldx, Y, ldy, D, m, n, ntj, sym, rps, P);
+  FD_LAUNCHED(ctx);
+  k_gram_reduce<<<(unsigned)cdiv((int64_t)m * n, 256), 256, 0, ctx->stream>>>(P, (int)slices, m, n,
+                                                                             sym, C, ldc);
+  FD_LAUNCHED(ctx);
+  return FD_OK;
+}
+
+fd_status identity_dev(fd_ctx* ctx, double* A, int n) {
+  k_identity<<<(unsigned)cdiv((int64_t)n * n, 256), 256, 0, ctx->stream>>>(A, n);
+  FD_LAUNCHED(ctx);
+  return FD_OK;
+}
+
+fd_status small_gemm_dev(fd_ctx* ctx, const double* A, const double* B, double* C, int n) {
+  k_small_gemm<<<(unsigned)cdiv((int64_t)n * n, 256), 256, 0, ctx->stream>>>(A, B, C, n);
+  FD_LAUNCHED(ctx);
+  return FD_OK;
+}
+
 fd_status rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M, bool upper) {
   const size_t smem = sizeof(double) * RT * n;
   if (smem > ctx->smem_optin) return set_err(ctx, FD_ERR_ARG, "block too wide for rotation (%d)", n);

@@ -104,6 +104,13 @@ fd_status kpm(fd_ctx* ctx, const fd_matrix* A, int n_moments, int R, uint64_t se
 // sym: X == Y, compute upper tiles and mirror.
 fd_status gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, int64_t ldy,
                int64_t D, int m, int n, double* C, int ldc, bool sym);
+// the same product with the caller's partial-sum buffer P (>= slices * m * n
+// doubles, at most max_slices slices); allocates nothing
+fd_status gram_partials(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                        int64_t D, int m, int n, double* C, int ldc, bool sym, double* P,
+                        int64_t max_slices);
+fd_status identity_dev(fd_ctx* ctx, double* A, int n);
+fd_status small_gemm_dev(fd_ctx* ctx, const double* A, const double* B, double* C, int n);
 // V (D x n, ldv) <- V * M, M n x n row-major; upper = M upper triangular
 fd_status rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M,
                  bool upper);
