@@ -6,13 +6,17 @@ disorder uniform in [-1, 1], seed 1), nb = 64 vectors per SpMMV block,
 Chebyshev degree 500, N_s = 384 search vectors (6 blocks; the paper uses
 N_s = 384 for N_t = 100, Table 6), window [-0.05, 0.05].
 
-One step = one outer FD iteration through the C ABI: the Chebyshev filter on
-all 6 blocks (6 x 500 fused steps), Cholesky-QR (2 passes), Rayleigh-Ritz
-(SpMMV, Gram, Jacobi, rotations) and the residual norms, read back to the host.
+One step = one outer FD iteration through the C ABI in the FP32-filter form
+the workload names: every 64-wide bundle is rounded to FP32, filtered with
+500 fused FP32 steps and widened back; then Cholesky-QR (2 passes),
+Rayleigh-Ritz (SpMMV, Gram, Jacobi, rotations) and the residual norms run in
+FP64 and are read back to the host.
 value = algorithmic filter bytes per step (Eq. EstimateT, kappa = 5) / step
-time, i.e. the sweep's HBM throughput with the orthogonalisation and
-Rayleigh-Ritz time charged to it.  The inputs (6.4 GB block, 0.5 GB matrix)
-exceed the 129 MB L2, so no flush is needed between steps.
+time: the sweep's HBM throughput with the orthogonalisation and Rayleigh-Ritz
+time charged to it.  The all-FP64 form of the same step is reported under
+"f64_form"; its fused step is bound by GB300's FP64 rate, not by HBM.  The
+inputs (6.4 GB block, 0.5 GB matrix) exceed the 129 MB L2, so no flush is
+needed between steps.
 
 `--impl reference` times the FP64 CPU oracle (scipy CSR SpMMV + NumPy) on a
 bounded sample of the same workload on the host cores.
@@ -41,6 +45,12 @@ WORKLOAD = {"workload": "anderson3d L=128 (2,097,152 rows) stencil, nb=64, degre
                         "one FD outer iteration (filter + CholQR2 + Rayleigh-Ritz + residuals)",
             "rows": L ** 3, "nnz_per_row": 7, "nb": NB, "degree": DEGREE, "ns": NS,
             "window": list(WINDOW), "l2_policy": "inputs larger than L2 (6.4 GB block)"}
+
+
+# GB300 FP64 peak (nominal 1.25 TFLOP/s; an FMA-loop probe on this machine measured 1.20)
+FP64_TFLOPS = 1.25
+# DRAM bytes (read + write) of one generic FP32 step from ncu, profiles/ (None if stale)
+TRAFFIC_F32 = None
 
 
 def filter_bytes(D, nnz, nb, n, Sx):
@@ -176,15 +186,24 @@ def run_gpu(args):
     AV = torch.empty_like(V)
     W1 = torch.empty((D, NB), dtype=torch.float64, device=dev)
     W2 = torch.empty_like(W1)
+    V32 = torch.empty((D, NB), dtype=torch.float32, device=dev)
+    W132 = torch.empty_like(V32)
+    W232 = torch.empty_like(V32)
     fd.fd_orthonormalize(ctx, V)
-    sweep_bytes = (NS // NB) * filter_bytes(D, nnz, NB, DEGREE, 8.0)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    sweep_bytes32 = (NS // NB) * filter_bytes(D, nnz, NB, DEGREE, 4.0)
+    sweep_bytes64 = (NS // NB) * filter_bytes(D, nnz, NB, DEGREE, 8.0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
 
-    def step(times=None):
+    def step(prec, times=None):
         if times is not None:
             ev[0].record(stream)
         for j in range(0, NS, NB):
-            fd.fd_filter(ctx, A, V[:, j:j + NB], mu, alpha, beta, W1, W2)
+            if prec == "f32":
+                fd.fd_copy_block(ctx, V[:, j:j + NB], V32)
+                fd.fd_filter(ctx, A, V32, mu, alpha, beta, W132, W232)
+                fd.fd_copy_block(ctx, V32, V[:, j:j + NB])
+            else:
+                fd.fd_filter(ctx, A, V[:, j:j + NB], mu, alpha, beta, W1, W2)
         if times is not None:
             ev[1].record(stream)
         fd.fd_orthonormalize(ctx, V)
@@ -195,29 +214,46 @@ def run_gpu(args):
             times.append((ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(ev[2])))
         return th, rho
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
-    launches0 = ctx.kernel_launches
-    times = []
-    with ClockSampler(local) as clk:
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for _ in range(args.steps):
-            step(times)
-        t1.record(stream)
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            step(prec)
         barrier()
-    launches = ctx.kernel_launches - launches0
-    total_ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = tt.item()
+        l0 = ctx.kernel_launches
+        times = []
+        with ClockSampler(local) as clk:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(steps):
+                step(prec, times)
+            t1.record(stream)
+            barrier()
+        total = t0.elapsed_time(t1)
+        if world > 1:
+            tt = torch.tensor([total], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total = tt.item()
+        return total, times, ctx.kernel_launches - l0, clk.summary()
+
+    total_ms, times, launches, clocks = timed("f32", args.steps, args.warmup)
     ms_per_step = total_ms / args.steps
-    value = world * sweep_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    value = world * sweep_bytes32 * args.steps / (total_ms * 1e-3) / 1e9
     filt_ms = sum(t[0] for t in times)
-    achieved = sweep_bytes * args.steps / (filt_ms * 1e-3) / 1e9
+    achieved = sweep_bytes32 * args.steps / (filt_ms * 1e-3) / 1e9
+
+    # all-FP64 form of the same step: FP64-ALU bound on GB300
+    k64 = max(1, min(2, args.steps))
+    total64, times64, _, _ = timed("f64", k64, 1)
+    filt64 = sum(t[0] for t in times64)
+    flops64 = (NS // NB) * DEGREE * (2.0 * nnz * NB + 6.0 * NB * D)
+    f64_form = {"value": world * sweep_bytes64 * k64 / (total64 * 1e-3) / 1e9, "unit": UNIT,
+                "ms_per_step": total64 / k64, "steps": k64,
+                "filter_gbs": sweep_bytes64 * k64 / (filt64 * 1e-3) / 1e9,
+                "roofline": {"bound": "alu", "achieved": flops64 * k64 / (filt64 * 1e-3) / 1e12,
+                             "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                             "frac": flops64 * k64 / (filt64 * 1e-3) / 1e12 / FP64_TFLOPS,
+                             "peak_source": "nominal GB300 FP64 rate of the profiling recipe "
+                                            "(an FMA-loop probe measured 1.20)"}}
 
     # e2e: the same step with the search block copied in from pinned host memory and
     # the Ritz values / residuals read back, all inside the timed region
@@ -228,11 +264,11 @@ def run_gpu(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         V.copy_(host, non_blocking=True)
-        step()
+        step("f32")
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_val = world * sweep_bytes / (statistics.mean(e2e_ms) * 1e-3) / 1e9
+    e2e_val = world * sweep_bytes32 / (statistics.mean(e2e_ms) * 1e-3) / 1e9
 
     # time to solution: 20 eigenpairs of the 8-site Hubbard chain at residual <= 1e-9
     A1 = fd.fd_build_matrix(ctx, "hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open")
@@ -259,17 +295,20 @@ def run_gpu(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": WORKLOAD,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "dtype_detail": "FP32 filter sweeps; FP64 Cholesky-QR, Rayleigh-Ritz, residuals",
+                "data": "synthetic", "config": WORKLOAD,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
-                             "kernel": "k_cheb_step (fused SpMMV + recurrence + accumulation)",
-                             "bytes_per_generic_launch": generic_step_bytes(D, nnz, NB, 8.0)},
+                             "frac": achieved / peak, "traffic": TRAFFIC_F32, "peak_source": peak_note,
+                             "kernel": "k_cheb_step<float,64> (fused SpMMV + recurrence + "
+                                       "accumulation), averaged over the filter phase",
+                             "bytes_per_generic_launch": generic_step_bytes(D, nnz, NB, 4.0)},
+                "f64_form": f64_form,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": D * NS * 8,
                         "d2h_bytes_per_step": 2 * NS * 8},
                 "gpu_launches": launches,
-                "clocks": clk.summary(),
+                "clocks": clocks,
                 "phases_ms_per_step": {"filter": filt_ms / args.steps,
                                        "ortho_rr": sum(t[1] - t[0] for t in times) / args.steps},
                 "time_to_solution": {"workload": "hubbard 8 sites 4+4 open, 20 eigenpairs nearest "
@@ -280,6 +319,123 @@ def run_gpu(args):
     return 0
 
 
+KERNEL_WORKLOADS = {
+    "stencil": SPEC,
+    "hubbard14": "hubbard:n_sites=14,n_up=7,n_dn=7,t=1,U=4,bc=periodic",
+    "roadgraph": "roadgraph:side=2000,q=0.3,seed=0",
+}
+
+
+def run_ozaki_probe(D=524288, ns=NS):
+    """Profiling driver of the dense steps: Cholesky-QR of a D x ns FP64 block with
+    the tensor-core (Ozaki) products and with FP64 arithmetic, timed; 1.5 GB."""
+    import torch
+
+    import paper_2209_01974_gb300 as fd
+    ctx = fd.fd_create(0)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    V0 = torch.randn((D, ns), dtype=torch.float64, device="cuda", generator=g)
+    out = {}
+    for mode in ("ozaki", "fp64"):
+        fd.fd_set_gemm_mode(ctx, mode)
+        V = V0.clone()
+        fd.fd_orthonormalize(ctx, V)
+        torch.cuda.synchronize()
+        V = V0.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fd.fd_orthonormalize(ctx, V)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        # two passes of Gram (D ns^2 symmetric) + triangular rotation (D ns^2 / 2)
+        flops = 2 * (D * ns * ns + D * ns * ns)
+        out[mode] = {"ms": ms, "fp64_equiv_tflops": flops / ms / 1e9}
+    print(json.dumps({"kernel_only": "cholqr2", "D": D, "ns": ns, **out}))
+    return 0
+
+
+def run_kernel_only(prec, workload="stencil", nb=NB):
+    """Profiling driver: one nb-wide block of a workload matrix (the L=128 stencil by
+    default; the 14-site Hubbard ring; the 4M-node road graph), degree-12 filters in
+    FP32 or FP64; used for the ncu captures summarised under profiles/."""
+    import torch
+
+    import paper_2209_01974_gb300 as fd
+    dt = torch.float64 if prec == "f64" else torch.float32
+    ctx = fd.fd_create(0)
+    A = fd.fd_build_matrix(ctx, KERNEL_WORKLOADS[workload])
+    D, nnz = A.D, A.info["nnz"]
+    lo, hi = fd.fd_spectral_bounds(ctx, A)
+    al, be = 2 / (hi - lo), -(hi + lo) / (hi - lo)
+    mu = fd.fd_filter_coeffs(al * WINDOW[0] + be, al * WINDOW[1] + be, 12)
+    V = torch.randn((D, nb), dtype=dt, device="cuda")
+    W1, W2 = torch.empty_like(V), torch.empty_like(V)
+    for _ in range(2):
+        fd.fd_filter(ctx, A, V, mu, al, be, W1, W2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        fd.fd_filter(ctx, A, V, mu, al, be, W1, W2)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5 / 12
+    es = 8.0 if prec == "f64" else 4.0
+    print(json.dumps({"kernel_only": prec, "workload": workload, "rows": D, "nnz": nnz, "nb": nb,
+                      "ms_per_step": ms,
+                      "gbs_generic_bytes": generic_step_bytes(D, nnz, nb, es) / ms / 1e6}))
+    return 0
+
+
+def run_batched(args):
+    """64 independent 3D Anderson instances (L = 16 + floor(33 u), W = 2 + 14 u from
+    SplitMix64 streams 5 / 6, seeds 0..63), 16 eigenpairs nearest E = 0, nb = 16,
+    degree >= 200, residual <= 1e-9: one batched solve (persistent filter launch
+    per outer iteration, CUDA graph, autotuned nb / C / CTA shape) against 64
+    sequential fd_solve calls."""
+    import torch
+
+    import paper_2209_01974_gb300 as fd
+    from fd_inputs import anderson_instance
+    n = args.instances
+    specs = []
+    for s in range(n):
+        L, W = anderson_instance(s)
+        specs.append(f"anderson3d:L={L},W={float(W)!r},seed={s}")
+    ctx = fd.fd_create(0)
+    t0 = time.perf_counter()
+    tune = fd.fd_tune_batched(ctx, specs, 16, 20)
+    t_tune = time.perf_counter() - t0
+    mats = [fd.fd_build_matrix(ctx, sp, C=tune["C"]) for sp in specs]
+    probs = [(-0.01, 0.01, 16, s) for s in range(n)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out, res = fd.fd_solve_batched(ctx, mats, probs, tune["nb"], 200, 1e-9, raise_noconv=False,
+                                   cta_warps=tune["cta_warps"], max_outer=args.max_outer,
+                                   n_max=args.n_max)
+    t_batched = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    seq = []
+    for m, (a, b, nt, sd) in zip(mats, probs):
+        th, rho, r = fd.fd_solve(ctx, m, a, b, nt, tune["nb"], 200, 1e-9, seed=sd, raise_noconv=False,
+                                 max_outer=args.max_outer, n_max=args.n_max)
+        seq.append(r)
+    t_seq = time.perf_counter() - t0
+    rows = sum(m.D for m in mats)
+    line = {"workload": f"batched: {n} Anderson instances L 16..48, W 2..16, 16 pairs at E=0, "
+                        "nb from tuner, degree >= 200, tol 1e-9",
+            "rows_total": rows, "tuner": tune, "tuner_seconds": t_tune,
+            "batched_seconds": t_batched, "sequential_seconds": t_seq,
+            "speedup": t_seq / t_batched,
+            "converged_batched": sum(r["converged"] for r in res),
+            "converged_sequential": sum(r["converged"] for r in seq),
+            "used_graph": res[0]["used_graph"],
+            "max_resid_batched": float(max((o[1].max() for o in out), default=0.0))}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,7 +443,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--kernel-only", choices=["f32", "f64", "cholqr2"], default=None,
+                    help="profiling driver: degree-12 filters on one nb-wide block")
+    ap.add_argument("--workload", choices=sorted(KERNEL_WORKLOADS), default="stencil")
+    ap.add_argument("--nb", type=int, default=NB)
+    ap.add_argument("--batched", action="store_true",
+                    help="batched-instances measurement (64 Anderson problems) instead of the bench")
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--max-outer", type=int, default=40)
+    ap.add_argument("--n-max", type=int, default=20000)
     args = ap.parse_args()
+    if args.batched:
+        return run_batched(args)
+    if args.kernel_only == "cholqr2":
+        return run_ozaki_probe()
+    if args.kernel_only:
+        return run_kernel_only(args.kernel_only, args.workload, args.nb)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -45,3 +45,21 @@ def random_symmetric_csr(D, mean_offdiag, seed, max_row=None, scale=1.0):
     rowptr = np.zeros(D + 1, dtype=np.int64)
     np.cumsum(counts, out=rowptr[1:])
     return rowptr, cols.astype(np.int32), summed.astype(np.float64)
+
+
+def _splitmix_uniform(seed, stream, i):
+    """u = (mix64(key + (i+1) gamma) >> 11) 2^-53, key = mix64(seed ^ mix64(stream)):
+    the SplitMix64 counter stream (Steele, Lea, Flood 2014) used for problem sizes."""
+    M = 2 ** 64
+
+    def mix(z):
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) % M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) % M
+        return z ^ (z >> 31)
+    key = mix(seed ^ mix(stream))
+    return (mix((key + (i + 1) * 0x9E3779B97F4A7C15) % M) >> 11) * 2.0 ** -53
+
+
+def anderson_instance(s):
+    """Size L in 16..48 and disorder W in [2, 16] of batched instance s (streams 5, 6)."""
+    return 16 + int(33.0 * _splitmix_uniform(s, 5, 0)), 2.0 + 14.0 * _splitmix_uniform(s, 6, 0)

@@ -173,6 +173,36 @@ fd_status fd_filter_coeffs(double x_l, double x_r, int n, double* mu);
 fd_status fd_spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec,
                    const void* X, int64_t ldx, void* Y, int64_t ldy, int nb);
 
+/* How the FP64 Gram and rotation products of fd_orthonormalize,
+ * fd_rayleigh_ritz and fd_solve are computed.
+ *   FD_GEMM_FP64   FP64 FMA arithmetic (GB300 runs FP64 at about 1/64 of FP32)
+ *   FD_GEMM_OZAKI  exact splitting into 7-bit integer digits on bf16 tensor
+ *                  cores (Ozaki scheme, 8 digits per operand relative to each
+ *                  row / column maximum, 128-bit integer accumulation): FP64
+ *                  accuracy at tensor-core speed
+ *   FD_GEMM_AUTO   Ozaki for D >= 65536 and at least 64 columns, else FP64
+ * Inputs holding NaN or infinity always take the FP64 path. */
+typedef enum { FD_GEMM_AUTO = 0, FD_GEMM_FP64 = 1, FD_GEMM_OZAKI = 2 } fd_gemm_mode;
+fd_status fd_set_gemm_mode(fd_ctx* ctx, fd_gemm_mode mode);
+
+/* Gram product C = X^T Y (device; X: D x m with ldx, Y: D x n with ldy, C: m x n
+ * row-major with ldc), the tall-skinny contraction of Cholesky-QR and
+ * Rayleigh-Ritz (Sec. 2).  X == Y (same pointer and ld, m == n) computes the
+ * upper tiles and mirrors them.  Arithmetic per fd_set_gemm_mode. */
+fd_status fd_gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                  int64_t D, int m, int n, double* C, int ldc);
+/* In-place rotation V <- V M (device; V: D x n with ldv, M: n x n row-major;
+ * upper != 0: M is upper triangular and its lower part is not read). */
+fd_status fd_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M,
+                    int upper);
+
+/* Copy the D x n device block src (leading dimension lds, type sp) into dst
+ * (ldd, type dp), rounding FP64 to FP32 or widening FP32 to FP64 as needed
+ * (the FP32 filter form moves bundles between the FP64 search block and FP32
+ * sweep buffers with this call). */
+fd_status fd_copy_block(fd_ctx* ctx, const void* src, fd_prec sp, int64_t lds, void* dst,
+                        fd_prec dp, int64_t ldd, int64_t D, int n);
+
 /* Orthonormalise the D x ns FP64 block V in place (Sec. 2: orthogonalisation
  * after the random start and after every filter application) by Cholesky-QR
  * twice (G = V^T V, G = R^T R, V <- V R^-1).  A Cholesky pivot that is not
@@ -205,8 +235,8 @@ fd_status fd_orthonormalize_noalloc(fd_ctx* ctx, double* V, int64_t D, int ns,
 
 /* Rayleigh-Ritz step (Sec. 2): for an orthonormal D x ns FP64 block V,
  * AV <- H V, Hs = V^T AV, Hs = Q diag(theta) Q^T (theta ascending, FP64
- * Jacobi on the device), V <- V Q, AV <- AV Q and resid_i = ||AV_i -
- * theta_i V_i||_2.  V and AV share the leading dimension ld.  theta and resid
+ * Jacobi on the device), V <- V Q, AV <- H V (a second SpMMV, cheaper than
+ * rotating AV) and resid_i = ||AV_i - theta_i V_i||_2.  V and AV share the leading dimension ld.  theta and resid
  * are HOST arrays of ns doubles.  Synchronises. */
 fd_status fd_rayleigh_ritz(fd_ctx* ctx, const fd_matrix* A, double* V,
                            double* AV, int64_t D, int ns, int64_t ld,

@@ -74,6 +74,10 @@ _SIGS = {
     "fd_filter": (_i32, [_vp, _vp, _i32, _vp, _i64, _i32, _i32, _pd, _dbl, _dbl, _vp, _vp, _i64]),
     "fd_filter_coeffs": (_i32, [_dbl, _dbl, _i32, _pd]),
     "fd_spmmv": (_i32, [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _i32]),
+    "fd_set_gemm_mode": (_i32, [_vp, _i32]),
+    "fd_gram": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _i32, _vp, _i32]),
+    "fd_rotate": (_i32, [_vp, _vp, _i64, _i64, _i32, _vp, _i32]),
+    "fd_copy_block": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _i64, _i64, _i32]),
     "fd_orthonormalize": (_i32, [_vp, _vp, _i64, _i32, _i64, _vp, ctypes.POINTER(_i32)]),
     "fd_orthonormalize_noalloc": (_i32, [_vp, _vp, _i64, _i32, _i64, _vp, ctypes.POINTER(_i32)]),
     "fd_rayleigh_ritz": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, _i64, _pd, _pd]),
@@ -265,6 +269,45 @@ def fd_spmmv(ctx, A, X, Y):
     if precy != prec:
         raise ValueError("X and Y must have the same dtype")
     _check(ctx, _lib.fd_spmmv(ctx.handle, A.handle, prec, _vp(px), ldx, _vp(py), ldy, nb))
+
+
+FD_GEMM_AUTO, FD_GEMM_FP64, FD_GEMM_OZAKI = 0, 1, 2
+
+
+def fd_set_gemm_mode(ctx, mode):
+    """mode: FD_GEMM_AUTO, FD_GEMM_FP64 or FD_GEMM_OZAKI (or 'auto'/'fp64'/'ozaki')."""
+    if isinstance(mode, str):
+        mode = {"auto": 0, "fp64": 1, "ozaki": 2}[mode]
+    _check(ctx, _lib.fd_set_gemm_mode(ctx.handle, mode))
+
+
+def fd_gram(ctx, X, Y):
+    """C = X^T Y for float64 CUDA blocks X (D x m) and Y (D x n); returns C (m x n)."""
+    import torch
+    px, ldx, D, m, _ = _block(X, "X")
+    py, ldy, D2, n, _ = _block(Y, "Y")
+    if D != D2:
+        raise ValueError("X and Y need the same number of rows")
+    C = torch.empty((m, n), dtype=torch.float64, device=X.device)
+    _check(ctx, _lib.fd_gram(ctx.handle, _vp(px), ldx, _vp(py), ldy, D, m, n, _vp(C.data_ptr()), n))
+    return C
+
+
+def fd_rotate(ctx, V, M, upper=False):
+    """V <- V M in place (V: D x n float64 CUDA block, M: n x n contiguous)."""
+    pv, ldv, D, n, _ = _block(V, "V")
+    if not M.is_contiguous() or tuple(M.shape) != (n, n):
+        raise ValueError("M must be a contiguous n x n tensor")
+    _check(ctx, _lib.fd_rotate(ctx.handle, _vp(pv), ldv, D, n, _vp(M.data_ptr()), 1 if upper else 0))
+
+
+def fd_copy_block(ctx, src, dst):
+    """dst <- src (same shape), converting between float64 and float32."""
+    ps, lds, D, n, sp = _block(src, "src")
+    pd, ldd, D2, n2, dp = _block(dst, "dst")
+    if (D, n) != (D2, n2):
+        raise ValueError("src and dst shapes differ")
+    _check(ctx, _lib.fd_copy_block(ctx.handle, _vp(ps), sp, lds, _vp(pd), dp, ldd, D, n))
 
 
 def fd_orthonormalize(ctx, V, R=None):

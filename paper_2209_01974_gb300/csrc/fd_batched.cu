@@ -119,7 +119,7 @@ __device__ __forceinline__ void batched_row_group(const BatchArgs& b, int t, int
 }
 
 template <int NB>
-__global__ void __launch_bounds__(WARPS * 32, MIN_BLOCKS) k_batched_filter(BatchArgs b) {
+__global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
   using L = Layout<double, NB>;
   extern __shared__ int64_t s_off[];  // n_tasks + 1
   for (int i = threadIdx.x; i <= b.n_tasks; i += blockDim.x) s_off[i] = b.task_off[i];
@@ -645,8 +645,7 @@ fd_status launch_ortho_rr(fd_ctx* ctx, Batch& B) {
   FD_LAUNCHED(ctx);
   k_brotate<<<rgrid, 256, rot_smem, st>>>(B.d_inst, B.d_par, 0, 0, 0);
   FD_LAUNCHED(ctx);
-  k_brotate<<<rgrid, 256, rot_smem, st>>>(B.d_inst, B.d_par, 1, 0, 0);
-  FD_LAUNCHED(ctx);
+  FD_TRY(launch_filter(ctx, B, 1));  // A (V Q) directly, cheaper than rotating AV
   k_bresid<<<dim3(RBLK, n), 128, 0, st>>>(B.d_inst, B.d_par);
   FD_LAUNCHED(ctx);
   k_bresid_reduce<<<n, 128, 0, st>>>(B.d_inst, B.d_par);

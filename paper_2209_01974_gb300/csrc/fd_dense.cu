@@ -389,8 +389,20 @@ __global__ void k_f32_to_f64(const float* s, int64_t lds, double* d, int64_t ldd
 
 }  // namespace
 
+// tall-skinny products large enough for the tensor-core splitting to pay off
+static bool use_ozaki(const fd_ctx* ctx, int64_t D, int m, int n) {
+  if (ctx->gemm_mode == FD_GEMM_FP64) return false;
+  if (ctx->gemm_mode == FD_GEMM_OZAKI) return true;
+  return D >= 65536 && m >= 64 && n >= 64;
+}
+
 fd_status gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t D,
                int m, int n, double* C, int ldc, bool sym) {
+  if (use_ozaki(ctx, D, m, n)) {
+    bool used = false;
+    FD_TRY(oz_gram(ctx, X, ldx, Y, ldy, D, m, n, C, ldc, sym, &used));
+    if (used) return FD_OK;
+  }
   const int nti = (int)cdiv(m, GT), ntj = (int)cdiv(n, GT);
   const int tiles = sym ? nti * (nti + 1) / 2 : nti * ntj;
   int64_t slices = std::max<int64_t>(1, cdiv(4LL * ctx->num_sms, tiles));
@@ -441,6 +453,11 @@ fd_status small_gemm_dev(fd_ctx* ctx, const double* A, const double* B, double* 
 }
 
 fd_status rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M, bool upper) {
+  if (use_ozaki(ctx, D, n, n)) {
+    bool used = false;
+    FD_TRY(oz_rotate(ctx, V, ldv, D, n, M, upper, &used));
+    if (used) return FD_OK;
+  }
   const size_t smem = sizeof(double) * RT * n;
   if (smem > ctx->smem_optin) return set_err(ctx, FD_ERR_ARG, "block too wide for rotation (%d)", n);
   if (smem > 48 * 1024)
@@ -571,7 +588,13 @@ fd_status rayleigh_ritz_dev(fd_ctx* ctx, const fd_matrix* A, double* V, double* 
   FD_TRY(gram(ctx, V, ld, AV, ld, D, ns, ns, H, ns, true));
   FD_TRY(sym_eig(ctx, H, ns, theta_dev, Q, 40));
   FD_TRY(rotate(ctx, V, ld, D, ns, Q, false));
-  FD_TRY(rotate(ctx, AV, ld, D, ns, Q, false));
+  // A (V Q) by a second SpMMV instead of rotating AV: on GB300 the rotation is
+  // FP64-ALU bound (D ns^2 FMAs) while the SpMMV costs nnz ns FMAs
+  for (int j = 0; j < ns;) {
+    int w = bundle_width(ns - j);
+    FD_TRY(spmmv(ctx, A, FD_F64, V + j, ld, AV + j, ld, w, true));
+    j += w;
+  }
   FD_TRY(resid_norms(ctx, V, AV, ld, D, ns, theta_dev, resid_dev));
   return FD_OK;
 }
@@ -603,6 +626,52 @@ fd_status fd_orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns, int64_t l
     return set_err(ctx, FD_ERR_ARG, "need V, 1 <= ns <= min(1024, D), ldv >= ns");
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
   return orthonormalize(ctx, V, D, ns, ldv, R, passes);
+}
+
+fd_status fd_gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t D,
+                   int m, int n, double* C, int ldc) {
+  if (!ctx) return FD_ERR_ARG;
+  ctx->err.clear();
+  if (!X || !Y || !C || D < 1 || m < 1 || n < 1 || m > 4096 || n > 4096 || ldx < m || ldy < n || ldc < n)
+    return set_err(ctx, FD_ERR_ARG, "need blocks, D >= 1, 1 <= m, n <= 4096, ld >= width");
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  return gram(ctx, X, ldx, Y, ldy, D, m, n, C, ldc, X == Y && ldx == ldy && m == n);
+}
+
+fd_status fd_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M, int upper) {
+  if (!ctx) return FD_ERR_ARG;
+  ctx->err.clear();
+  if (!V || !M || D < 1 || n < 1 || n > 1024 || ldv < n)
+    return set_err(ctx, FD_ERR_ARG, "need blocks, D >= 1, 1 <= n <= 1024, ldv >= n");
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  return rotate(ctx, V, ldv, D, n, M, upper != 0);
+}
+
+fd_status fd_set_gemm_mode(fd_ctx* ctx, fd_gemm_mode mode) {
+  if (!ctx) return FD_ERR_ARG;
+  if (mode != FD_GEMM_AUTO && mode != FD_GEMM_FP64 && mode != FD_GEMM_OZAKI)
+    return set_err(ctx, FD_ERR_ARG, "unknown gemm mode %d", (int)mode);
+  ctx->gemm_mode = (int)mode;
+  return FD_OK;
+}
+
+fd_status fd_copy_block(fd_ctx* ctx, const void* src, fd_prec sp, int64_t lds, void* dst, fd_prec dp,
+                        int64_t ldd, int64_t D, int n) {
+  if (!ctx) return FD_ERR_ARG;
+  ctx->err.clear();
+  if (!src || !dst || D < 0 || n < 0 || lds < n || ldd < n || (sp != FD_F64 && sp != FD_F32) ||
+      (dp != FD_F64 && dp != FD_F32))
+    return set_err(ctx, FD_ERR_ARG, "need buffers, D, n >= 0, lds, ldd >= n and FD_F64/FD_F32");
+  if (D == 0 || n == 0) return FD_OK;
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (sp == FD_F64 && dp == FD_F32)
+    return copy_cols_f64_to_f32(ctx, (const double*)src, lds, (float*)dst, ldd, D, n);
+  if (sp == FD_F32 && dp == FD_F64)
+    return copy_cols_f32_to_f64(ctx, (const float*)src, lds, (double*)dst, ldd, D, n);
+  const size_t es = sp == FD_F64 ? 8 : 4;
+  FD_CUDA(ctx, cudaMemcpy2DAsync(dst, ldd * es, src, lds * es, n * es, D, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+  return FD_OK;
 }
 
 fd_status fd_rayleigh_ritz(fd_ctx* ctx, const fd_matrix* A, double* V, double* AV, int64_t D, int ns,

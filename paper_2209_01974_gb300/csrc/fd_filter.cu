@@ -26,7 +26,7 @@ namespace {
 using namespace step;
 
 template <typename T, int NB, int MODE>
-__global__ void __launch_bounds__(WARPS * 32, MIN_BLOCKS)
+__global__ void __launch_bounds__(WARPS * 32, sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64)
     k_cheb_step(SellArgs<T> A, StepArgs<T> s) {
   using L = Layout<T, NB>;
   const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
@@ -198,7 +198,7 @@ __global__ void k_kpm_init(double* r, int64_t D, int R, const int64_t* perm, uin
 // one step: x_new = c_ax * A x + c_x * x [- z]; partial[blk] = (sum x_new . x, sum x_new . x_new,
 // sum x . x); grid-stride over rows so the number of partials is fixed
 template <int NB, bool FIRST>
-__global__ void __launch_bounds__(WARPS * 32, MIN_BLOCKS)
+__global__ void __launch_bounds__(WARPS * 32, 4)
     k_kpm_step(SellArgs<double> A, const double* X, const double* Z, double* Y, double c_ax,
                double c_x, double* partial) {
   using L = Layout<double, NB>;

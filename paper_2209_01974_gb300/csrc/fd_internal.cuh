@@ -19,6 +19,7 @@ struct fd_ctx {
   size_t smem_optin = 0;
   std::string err;
   int64_t launches = 0;
+  int gemm_mode = 0;  // fd_gemm_mode: 0 auto, 1 FP64 arithmetic, 2 bf16 tensor-core splitting
   // grow-only device workspaces keyed by purpose
   std::unordered_map<std::string, std::pair<void*, size_t>> ws;
   // pinned host staging
@@ -130,6 +131,12 @@ fd_status orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns, int64_t ldv,
 fd_status rayleigh_ritz_dev(fd_ctx* ctx, const fd_matrix* A, double* V, double* AV,
                             int64_t D, int ns, int64_t ld, double* theta_dev,
                             double* resid_dev);
+// Ozaki-scheme products on bf16 tensor cores (fd_ozaki.cu); *used = false
+// (and no error) when the input holds non-finite values
+fd_status oz_gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, int64_t ldy, int64_t D,
+                  int m, int n, double* C, int ldc, bool sym, bool* used);
+fd_status oz_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M, bool upper,
+                    bool* used);
 // small helpers
 fd_status copy_cols_f64_to_f32(fd_ctx* ctx, const double* src, int64_t lds, float* dst,
                                int64_t ldd, int64_t D, int n);

@@ -82,8 +82,9 @@ struct StepArgs {
 };
 
 constexpr int WARPS = 8;
-constexpr int BATCH = 8;   // entries per batch; SELL chunk lengths are multiples of 8
-constexpr int MIN_BLOCKS = 4;  // >= 32 resident warps per SM (<= 64 registers)
+constexpr int BATCH = 4;   // entries per batch; SELL chunk lengths are multiples of 8
+constexpr int MIN_BLOCKS = 6;  // FP32 steps: >= 48 resident warps per SM (<= 40 registers)
+constexpr int MIN_BLOCKS_F64 = 4;  // FP64 steps keep 64 registers (FP64-ALU bound anyway)
 
 template <typename T, int NB>
 struct Layout {

@@ -1,0 +1,116 @@
+"""FP64 Gram and rotation products on bf16 tensor cores (Ozaki splitting) against
+FP64 references, and the CholQR / Rayleigh-Ritz steps built on them."""
+import numpy as np
+import pytest
+
+import fd_inputs
+from oracle import matrices as mat
+from oracle import ortho, rayleigh_ritz
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def fd():
+    import paper_2209_01974_gb300 as fd
+    return fd
+
+
+@pytest.fixture(scope="module")
+def ctx(fd):
+    c = fd.fd_create(0)
+    yield c
+    fd.fd_set_gemm_mode(c, "auto")
+
+
+def _t(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _block(D, n, seed, spread=6):
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((D, n)) * np.logspace(0, spread, n)[None, :]
+    V[rng.random((D, n)) < 0.05] = 0.0
+    return V
+
+
+def _bound(X, Y):
+    # split error <= K * 2^-56 * (4 |X|max |Y|max) per entry, the reference's own
+    # rounding <= K u sum |x||y| <= K u |X|max |Y|max: both under 8 K u |X|max |Y|max
+    K = X.shape[0]
+    return 8 * K * U * np.outer(np.abs(X).max(0), np.abs(Y).max(0))
+
+
+@pytest.mark.parametrize("D,m,n", [(20000, 96, 96), (7777, 130, 70), (300, 64, 64)])
+def test_ozaki_gram_is_fp64_accurate(fd, ctx, D, m, n):
+    X = _block(D, m, 1)
+    Y = X if m == n else _block(D, n, 2, 3)
+    fd.fd_set_gemm_mode(ctx, "ozaki")
+    C = fd.fd_gram(ctx, _t(X), _t(Y)).cpu().numpy()
+    ref = X.T @ Y
+    assert np.all(np.abs(C - ref) <= _bound(X, Y))
+    # relative to what FP64 FMA arithmetic achieves on the same data
+    fd.fd_set_gemm_mode(ctx, "fp64")
+    C64 = fd.fd_gram(ctx, _t(X), _t(Y)).cpu().numpy()
+    assert np.all(np.abs(C64 - ref) <= _bound(X, Y))
+
+
+@pytest.mark.parametrize("upper", [False, True])
+def test_ozaki_rotation_is_fp64_accurate(fd, ctx, upper):
+    D, n = 9001, 96
+    V = _block(D, n, 3, 4)
+    M = np.random.default_rng(4).standard_normal((n, n)) * np.logspace(0, 3, n)[:, None]
+    if upper:
+        M = np.triu(M)
+    ref = V @ M
+    fd.fd_set_gemm_mode(ctx, "ozaki")
+    Vt = _t(V)
+    fd.fd_rotate(ctx, Vt, _t(M), upper)
+    got = Vt.cpu().numpy()
+    bound = 8 * n * U * np.outer(np.abs(V).max(1), np.abs(M).max(0))
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+def test_ozaki_cholqr_and_rr_match_fp64_mode(fd, ctx):
+    import torch
+    D, ns = 30000, 64
+    V0 = fd_inputs.random_block(D, ns, 9) @ np.diag(np.logspace(0, 4, ns))
+    out = {}
+    for mode in ("fp64", "ozaki"):
+        fd.fd_set_gemm_mode(ctx, mode)
+        V = _t(V0)
+        R = torch.zeros((ns, ns), dtype=torch.float64, device="cuda")
+        assert fd.fd_orthonormalize(ctx, V, R) == 2
+        Q = V.cpu().numpy()
+        assert np.abs(Q.T @ Q - np.eye(ns)).max() < 1e-14
+        out[mode] = (Q, R.cpu().numpy())
+    assert np.abs(out["fp64"][0] - out["ozaki"][0]).max() < 1e-10
+    assert np.abs(out["fp64"][1] - out["ozaki"][1]).max() < 1e-12 * np.abs(out["fp64"][1]).max()
+    Qo, Ro, _ = ortho.cholqr2(V0)
+    assert np.abs(out["ozaki"][1] - Ro).max() <= 1e-12 * np.abs(Ro).max()
+
+
+def test_ozaki_rayleigh_ritz(fd, ctx):
+    import torch
+    spec = "anderson3d:L=40,W=4,seed=3"
+    csr = mat.build(spec)
+    D = 40 ** 3
+    V0, _ = np.linalg.qr(fd_inputs.random_block(D, 64, 5))
+    A = fd.fd_build_matrix(ctx, spec)
+    fd.fd_set_gemm_mode(ctx, "ozaki")
+    V = _t(V0)
+    th, rho = fd.fd_rayleigh_ritz(ctx, A, V, torch.empty_like(V))
+    tho, _, _, rhoo = rayleigh_ritz.rayleigh_ritz(mat.to_scipy(csr), V0)
+    assert np.abs(th - tho).max() <= 1e-12 * np.abs(tho).max()
+    assert np.abs(rho - rhoo).max() <= 1e-11 * np.abs(tho).max()
+
+
+def test_ozaki_nonfinite_input_takes_fp64_path(fd, ctx):
+    fd.fd_set_gemm_mode(ctx, "ozaki")
+    bad = fd_inputs.random_block(5000, 64, 1)
+    bad[7, 3] = np.nan
+    with pytest.raises(fd.FDError) as e:
+        fd.fd_orthonormalize(ctx, _t(bad))
+    assert e.value.status == fd.FD_ERR_BREAKDOWN

@@ -173,3 +173,9 @@ def test_roadgraph_is_a_connected_planar_laplacian():
     ev = np.linalg.eigvalsh(A.toarray())
     assert abs(ev[0]) < 1e-10 and ev[1] > 1e-6                       # one zero mode: connected
     assert ev[-1] <= 8.0 + 1e-12                                     # Gershgorin: 2 * max degree
+
+
+def test_instance_sizes_agree_with_input_generator():
+    import fd_inputs
+    for s in range(64):
+        assert fd_inputs.anderson_instance(s) == mat.anderson_instance(s)
