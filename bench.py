@@ -153,6 +153,24 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(value, world, device="cpu"):
+    """Largest value over all ranks (the job's time is its slowest replica's)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(bytes_per_rank_step, steps, world, max_ms):
+    """Whole-job GB/s of `world` independent replicas (weak scaling): all ranks'
+    algorithmic bytes over the slowest rank's time."""
+    return world * bytes_per_rank_step * steps / (max_ms * 1e-3) / 1e9
+
+
 # --------------------------------------------------------------------------- GPU leg
 def run_gpu(args):
     import torch
@@ -228,16 +246,12 @@ def run_gpu(args):
                 step(prec, times)
             t1.record(stream)
             barrier()
-        total = t0.elapsed_time(t1)
-        if world > 1:
-            tt = torch.tensor([total], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total = tt.item()
+        total = max_over_ranks(t0.elapsed_time(t1), world, dev)
         return total, times, ctx.kernel_launches - l0, clk.summary()
 
     total_ms, times, launches, clocks = timed("f32", args.steps, args.warmup)
     ms_per_step = total_ms / args.steps
-    value = world * sweep_bytes32 * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_throughput(sweep_bytes32, args.steps, world, total_ms)
     filt_ms = sum(t[0] for t in times)
     achieved = sweep_bytes32 * args.steps / (filt_ms * 1e-3) / 1e9
 
@@ -246,7 +260,7 @@ def run_gpu(args):
     total64, times64, _, _ = timed("f64", k64, 1)
     filt64 = sum(t[0] for t in times64)
     flops64 = (NS // NB) * DEGREE * (2.0 * nnz * NB + 6.0 * NB * D)
-    f64_form = {"value": world * sweep_bytes64 * k64 / (total64 * 1e-3) / 1e9, "unit": UNIT,
+    f64_form = {"value": job_throughput(sweep_bytes64, k64, world, total64), "unit": UNIT,
                 "ms_per_step": total64 / k64, "steps": k64,
                 "filter_gbs": sweep_bytes64 * k64 / (filt64 * 1e-3) / 1e9,
                 "roofline": {"bound": "alu", "achieved": flops64 * k64 / (filt64 * 1e-3) / 1e12,
@@ -436,6 +450,50 @@ def run_batched(args):
     return 0
 
 
+def pick_interior_window(mu, lam_l, lam_r, lo_frac=0.3, hi_frac=0.7, grid=4001):
+    """Centre of the lowest Jackson-damped KPM density between the given fractions
+    of the spectrum (a sparse region keeps the required degree moderate)."""
+    n = len(mu) - 1
+    N = n + 1
+    k = np.arange(n + 1)
+    a = np.pi / (N + 1)
+    g = ((N - k + 1) * np.cos(a * k) + np.sin(a * k) / np.tan(a)) / (N + 1)
+    x = np.linspace(-1 + 2 * lo_frac, -1 + 2 * hi_frac, grid)
+    T = np.cos(np.outer(np.arccos(x), k))
+    c = g * mu
+    c[1:] *= 2.0
+    dos = (T @ c) / (np.pi * np.sqrt(1 - x * x))
+    xc = x[np.argmin(dos)]
+    return 0.5 * (lam_r - lam_l) * xc + 0.5 * (lam_r + lam_l)
+
+
+def run_learned_eval(args):
+    """The trained filter-parameter predictor against the plain heuristic on the
+    road-like graph Laplacian: 64 eigenpairs at the sparsest interior point of its
+    KPM density, FP32 sweeps with FP64 finish, residual <= 1e-9."""
+    import paper_2209_01974_gb300 as fd
+    from paper_2209_01974_gb300 import predictor
+    ctx = fd.fd_create(0)
+    spec = f"roadgraph:side={args.side},q=0.3,seed=0"
+    A = fd.fd_build_matrix(ctx, spec)
+    lo, hi = fd.fd_spectral_bounds(ctx, A)
+    al, be = 2 / (hi - lo), -(hi + lo) / (hi - lo)
+    mu = fd.fd_kpm_moments(ctx, A, 256, 16, 0, al, be)
+    tau = pick_interior_window(mu, lo, hi)
+    params = predictor.load()
+    rows = {}
+    for name, p in (("heuristic", None), ("learned", params)):
+        th, rho, res, pred = predictor.solve_with(ctx, p, A, tau - 1e-3, tau + 1e-3, 64, 64, 100, 1e-9,
+                                                  seed=0, precision="f32", max_outer=args.max_outer,
+                                                  n_max=args.n_max)
+        rows[name] = {"converged": res["converged"], "iterations": res["iterations"],
+                      "n_spmmv": res["n_spmmv"], "final_degree": res["final_degree"],
+                      "seconds": res["t_total"], "max_resid": float(rho.max()), "params": pred}
+    print(json.dumps({"workload": f"{spec} ({A.D} nodes), 64 eigenpairs nearest {tau:.6f}, nb=64, "
+                                  "FP32 sweeps + FP64 finish, tol 1e-9", **rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,7 +510,12 @@ def main():
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--max-outer", type=int, default=40)
     ap.add_argument("--n-max", type=int, default=20000)
+    ap.add_argument("--learned-eval", action="store_true",
+                    help="predictor vs heuristic on the road-like graph Laplacian")
+    ap.add_argument("--side", type=int, default=400)
     args = ap.parse_args()
+    if args.learned_eval:
+        return run_learned_eval(args)
     if args.batched:
         return run_batched(args)
     if args.kernel_only == "cholqr2":

@@ -81,3 +81,24 @@ def test_noconv_reports_status(fd, ctx):
     assert e.value.status == fd.FD_ERR_NOCONV
     th, rho, res = fd.fd_solve(ctx, A, -0.5, 0.5, 20, 32, 10, 1e-9, max_outer=2, raise_noconv=False)
     assert res["converged"] == 0 and res["iterations"] == 2
+
+
+def test_fig2_diagonal_matrix_on_gpu(fd, ctx):
+    """The example of Fig. 2: 1000 equidistant eigenvalues in [-1, 1], the 10
+    nearest the centre of [-0.01, 0.01] with N_s = 20 search vectors."""
+    lam = -1 + 2 * np.arange(1000) / 999
+    A = fd.fd_matrix_from_csr(ctx, *mat.diagonal(lam))
+    th, rho, res = fd.fd_solve(ctx, A, -0.01, 0.01, 10, 4, 20, 1e-9, ns=20)
+    assert res["converged"] == 1 and rho.max() <= 1e-9
+    assert np.abs(th - _nearest(lam, 0.0, 10)).max() <= 1e-12
+
+
+def test_solve_rejects_degenerate_sizes(fd, ctx):
+    A = fd.fd_build_matrix(ctx, "chain:n=10")
+    with pytest.raises(fd.FDError) as e:
+        fd.fd_solve(ctx, A, -0.1, 0.1, 8, 16, 20, 1e-9)        # N_s = 32 > D = 10
+    assert e.value.status == fd.FD_ERR_ARG
+    with pytest.raises(fd.FDError):
+        fd.fd_solve(ctx, A, 0.1, -0.1, 2, 2, 20, 1e-9)         # a > b
+    with pytest.raises(fd.FDError):
+        fd.fd_matrix_from_csr(ctx, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))  # D = 0
