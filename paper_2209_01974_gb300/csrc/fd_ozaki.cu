@@ -6,18 +6,19 @@
 // "Error-free transformations of matrix multiplication", Numer. Algorithms
 // 2012; Mukunoki et al. 2020 on tensor cores):
 //
-//   a_ik = 2^{e_i} sum_{s<8} d^a_{s,ik} 2^{-7(s+1)},  |d| <= 127 (7-bit digits)
-//   b_kj = 2^{f_j} sum_{t<8} d^b_{t,kj} 2^{-7(t+1)}
-//   (AB)_ij = 2^{e_i + f_j} sum_{l<8} 2^{-7(l+2)} sum_{s+t=l} sum_k d^a_s d^b_t
+//   a_ik = 2^{e_i} sum_{s<7} d^a_{s,ik} 2^{-8(s+1)},  |d| <= 255 (8-bit digits)
+//   b_kj = 2^{f_j} sum_{t<7} d^b_{t,kj} 2^{-8(t+1)}
+//   (AB)_ij = 2^{e_i + f_j} sum_{l<7} 2^{-8(l+2)} sum_{s+t=l} sum_k d^a_s d^b_t
 //
 // with e_i (f_j) the exponent of the largest |a_ik| over k (|b_kj| over k), so
 // each operand is cut to 56 bits relative to its row (column) maximum, and the
-// pairs s + t >= 8 (weight <= 2^-70) are dropped.  Every digit is an integer
-// below 2^7 and therefore exact in bf16; a level l sums at most 8 pairs over a
-// K chunk of 64, all partial sums stay below 8 * 64 * 2^14 = 2^23 and the FP32
-// accumulation of mma.sync.m16n8k16 is exact.  Each level's chunk sum is then
-// converted to an integer and added, shifted by 7 (7 - l) bits, into a 128-bit
-// integer accumulator, which is exact; one conversion to FP64 at the end.
+// pairs s + t >= 7 (weight <= 2^-72) are dropped.  Every digit is an integer of
+// magnitude below 2^8 and therefore exact in bf16; a level l sums at most 7
+// pairs over a K chunk of 32, all partial sums stay below 7 * 32 * 255^2 <
+// 2^24 and the FP32 accumulation of mma.sync.m16n8k16 is exact.  Each level's
+// chunk sum is converted to an integer and added, scaled by 2^(8 (6 - l)), into
+// two 64-bit integer accumulators (levels 0-2 and 3-6), which is exact for up
+// to 2^14 chunks per CTA; one conversion to FP64 at the end.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -29,31 +30,26 @@
 namespace fdi {
 namespace {
 
-constexpr int OZ_S = 8;            // digits per operand
-constexpr int OZ_B = 7;            // bits per digit
+constexpr int OZ_S = 7;            // digits per operand
+constexpr int OZ_B = 8;            // bits per digit
 constexpr int OZ_F = OZ_S * OZ_B;  // 56 fraction bits
-constexpr int TB = 64;             // CTA tile (rows and columns) and K chunk
-constexpr int SK = TB + 8;         // padded K stride of a digit row (bf16 elements)
+constexpr int TB = 64;             // CTA tile (rows and columns)
+constexpr int KC = 32;             // K chunk
+constexpr int SK = KC + 8;         // padded K stride of a digit row (bf16 elements; 80 bytes)
 constexpr int OZ_THREADS = 256;
-constexpr size_t OZ_SMEM = sizeof(__nv_bfloat16) * 2 * OZ_S * TB * SK;  // 147,456 bytes
+constexpr size_t OZ_SMEM = sizeof(__nv_bfloat16) * 2 * OZ_S * TB * SK;  // 71,680 bytes
+constexpr int64_t OZ_MAX_CHUNKS = 1 << 14;  // per CTA, keeps the 64-bit accumulators exact
 
-// 8 signed 7-bit digits of x relative to 2^e (|x| < 2^e); zero for x == 0
-__device__ __forceinline__ void digits(double x, int e, int (&d)[OZ_S]) {
+// fixed-point magnitude y = |x| 2^(56 - e) (< 2^56 for |x| < 2^e) and sign of x
+__device__ __forceinline__ unsigned long long fixed56(double x, int e, bool* neg) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
   if (ex) m |= 1ull << 52;
   const int sh = (ex ? ex : 1) - 1075 - e + OZ_F;  // |x| 2^(F - e) = m 2^sh < 2^56
-  unsigned long long y;
-  if (m == 0 || sh <= -64) y = 0;
-  else if (sh >= 0) y = m << sh;
-  else y = m >> (-sh);
-  const bool neg = (bits >> 63) != 0;
-#pragma unroll
-  for (int s = 0; s < OZ_S; ++s) {
-    const int v = (int)((y >> (OZ_F - OZ_B * (s + 1))) & 0x7F);
-    d[s] = neg ? -v : v;
-  }
+  *neg = (bits >> 63) != 0;
+  if (m == 0 || sh <= -64) return 0;
+  return sh >= 0 ? m << sh : m >> (-sh);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
@@ -61,19 +57,25 @@ __device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
   return *reinterpret_cast<uint32_t*>(&p);
 }
 
-// store the digits of 8 consecutive K values of one row (of A or B) as 8 slices
+__device__ __forceinline__ int digit(unsigned long long y, bool neg, int s) {
+  const int v = (int)((y >> (OZ_F - OZ_B * (s + 1))) & 0xFF);
+  return neg ? -v : v;
+}
+
+// store the 7 digit slices of 8 consecutive K values of one row (of A or B)
 __device__ __forceinline__ void store_digits8(__nv_bfloat16* base_slice0, int row,
                                               const double (&x)[8], int e) {
-  int d[8][OZ_S];
+  unsigned long long y[8];
+  bool ng[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) digits(x[q], e, d[q]);
+  for (int q = 0; q < 8; ++q) y[q] = fixed56(x[q], e, &ng[q]);
 #pragma unroll
   for (int s = 0; s < OZ_S; ++s) {
     uint4 v;
-    v.x = pack_bf16x2(d[0][s], d[1][s]);
-    v.y = pack_bf16x2(d[2][s], d[3][s]);
-    v.z = pack_bf16x2(d[4][s], d[5][s]);
-    v.w = pack_bf16x2(d[6][s], d[7][s]);
+    v.x = pack_bf16x2(digit(y[0], ng[0], s), digit(y[1], ng[1], s));
+    v.y = pack_bf16x2(digit(y[2], ng[2], s), digit(y[3], ng[3], s));
+    v.z = pack_bf16x2(digit(y[4], ng[4], s), digit(y[5], ng[5], s));
+    v.w = pack_bf16x2(digit(y[6], ng[6], s), digit(y[7], ng[7], s));
     *reinterpret_cast<uint4*>(base_slice0 + (size_t)s * TB * SK + (size_t)row * SK) = v;
   }
 }
@@ -96,11 +98,17 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Exact accumulator of one output.  Level l carries the weight 2^(8 (6 - l))
+// in units of 2^-64 (relative to 2^(e_i + f_j)); value = hi 2^32 + lo.
+struct Acc {
+  long long hi, lo;  // levels 0-2 (weights 2^16, 2^8, 1) and 3-6 (2^24 .. 1)
+};
+
 // Tensor-core part of one K chunk: digits of A (rows) in As[s][m][k], of B
-// (columns) in Bs[t][n][k]; every level's exact sum goes into acc (128-bit).
+// (columns) in Bs[t][n][k]; every level's exact sum goes into acc.
 // Warp w covers rows (w & 3) * 16 .. +16 and columns (w >> 2) * 32 .. +32.
 __device__ __forceinline__ void chunk_mma(const __nv_bfloat16* As, const __nv_bfloat16* Bs,
-                                          __int128 (&acc)[4][4]) {
+                                          Acc (&acc)[4][4]) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = (w & 3) * 16, n0 = (w >> 2) * 32;
   // ldmatrix row addresses: A x4 -> (rows m0 + lane%16, k + 8*(lane/16)); B x2 -> (n + lane%8, k + 8*((lane/8)&1))
@@ -115,7 +123,7 @@ __device__ __forceinline__ void chunk_mma(const __nv_bfloat16* As, const __nv_bf
       const __nv_bfloat16* Asl = As + (size_t)s * TB * SK;
       const __nv_bfloat16* Bsl = Bs + (size_t)t * TB * SK;
 #pragma unroll
-      for (int kk = 0; kk < TB; kk += 16) {
+      for (int kk = 0; kk < KC; kk += 16) {
         uint32_t a[4];
         ldsm_x4(a, Asl + (size_t)ar * SK + kk + ak);
 #pragma unroll
@@ -126,23 +134,29 @@ __device__ __forceinline__ void chunk_mma(const __nv_bfloat16* As, const __nv_bf
         }
       }
     }
-    const __int128 wl = (__int128)1 << (OZ_B * (OZ_S - 1 - l));  // level weight 2^(7 (7 - l))
+    // level weight 2^(8 (6 - l)): levels 0-2 go to hi (scaled by 2^-32), 3-6 to lo
+    const bool to_hi = l < 3;
+    const int sh = to_hi ? 8 * (2 - l) : 8 * (6 - l);
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[nt][q] += (__int128)__float2ll_rn(c[nt][q]) * wl;
+      for (int q = 0; q < 4; ++q) {
+        const long long v = (long long)__float2int_rn(c[nt][q]) * (1ll << sh);
+        if (to_hi) acc[nt][q].hi += v;
+        else acc[nt][q].lo += v;
+      }
   }
 }
 
-__device__ __forceinline__ double i128_to_double(__int128 v) {
-  const long long hi = (long long)(v >> 64);
-  const unsigned long long lo = (unsigned long long)v;
-  return fma((double)hi, 0x1.0p64, (double)lo);
+__device__ __forceinline__ double acc_value(const Acc& a) {
+  // per chunk |hi| < 2^38 and |lo| < 2^48, so over 2^14 chunks hi stays exact
+  // in FP64 and lo in int64; the sum is rounded once
+  return fma((double)a.hi, 0x1.0p32, (double)a.lo);
 }
 
-// value of accumulator entry (nt, q) at global position, scaled by 2^(e_i + f_j - 63)
+// value of accumulator entry (nt, q) at its tile position, in units of 2^-64
 template <typename F>
-__device__ __forceinline__ void for_each_out(const __int128 (&acc)[4][4], F&& f) {
+__device__ __forceinline__ void for_each_out(const Acc (&acc)[4][4], F&& f) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = (w & 3) * 16, n0 = (w >> 2) * 32;
   const int g = lane >> 2, t4 = lane & 3;
@@ -152,7 +166,7 @@ __device__ __forceinline__ void for_each_out(const __int128 (&acc)[4][4], F&& f)
     for (int q = 0; q < 4; ++q) {
       const int i = m0 + g + (q >= 2 ? 8 : 0);
       const int j = n0 + nt * 8 + t4 * 2 + (q & 1);
-      f(i, j, i128_to_double(acc[nt][q]));
+      f(i, j, acc_value(acc[nt][q]));
     }
 }
 
@@ -202,7 +216,7 @@ __global__ void k_row_exp(const double* V, int64_t ld, int64_t D, int n, int* ex
 // ---------------------------------------------------------------------------
 // Gram: P[slice][i][j] = sum over the slice's rows k of X[k][i] Y[k][j]
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+__global__ void __launch_bounds__(OZ_THREADS, 2)
     k_oz_gram(const double* __restrict__ X, int64_t ldx, const double* __restrict__ Y, int64_t ldy,
               int64_t D, int m, int n, int ntj, int sym, int64_t rows_per_slice, const int* ex,
               const int* ey, double* __restrict__ P) {
@@ -222,15 +236,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int i0 = ti * TB, j0 = tj * TB;
   const int64_t k0 = (int64_t)blockIdx.y * rows_per_slice;
   const int64_t k1 = min(D, k0 + rows_per_slice);
-  __int128 acc[4][4];
+  Acc acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-  for (int64_t kb = k0; kb < k1; kb += TB) {
-    // digits: work item = (operand, column c, 8 consecutive k); 2 x 64 x 8 items
-    for (int item = threadIdx.x; item < 2 * TB * 8; item += OZ_THREADS) {
-      const int op = item / (TB * 8), rem = item % (TB * 8);
+    for (int b = 0; b < 4; ++b) acc[a][b] = Acc{0, 0};
+  for (int64_t kb = k0; kb < k1; kb += KC) {
+    // digits: work item = (operand, column c, 8 consecutive k); 2 x 64 x 4 items
+    for (int item = threadIdx.x; item < 2 * TB * (KC / 8); item += OZ_THREADS) {
+      const int op = item / (TB * (KC / 8)), rem = item % (TB * (KC / 8));
       const int c = rem % TB, kg = rem / TB;
       const int col = (op == 0 ? i0 : j0) + c;
       const int lim = op == 0 ? m : n;
@@ -252,7 +266,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   double* Ps = P + (int64_t)blockIdx.y * m * n;
   for_each_out(acc, [&](int i, int j, double v) {
     const int gi = i0 + i, gj = j0 + j;
-    if (gi < m && gj < n) Ps[(int64_t)gi * n + gj] = ldexp(v, ex[gi] + ey[gj] - 63);
+    if (gi < m && gj < n) Ps[(int64_t)gi * n + gj] = ldexp(v, ex[gi] + ey[gj] - 64);
   });
 }
 
@@ -284,22 +298,23 @@ __global__ void k_m_digits(const double* M, int n, int npad, const int* em, __nv
     const int k = kg * 8 + q;
     x[q] = (j < n && k < n) ? M[(int64_t)k * n + j] : 0.0;
   }
-  int d[8][OZ_S];
   const int e = j < n ? em[j] : 0;
+  unsigned long long y[8];
+  bool ng[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) digits(x[q], e, d[q]);
+  for (int q = 0; q < 8; ++q) y[q] = fixed56(x[q], e, &ng[q]);
 #pragma unroll
   for (int s = 0; s < OZ_S; ++s) {
     uint4 v;
-    v.x = pack_bf16x2(d[0][s], d[1][s]);
-    v.y = pack_bf16x2(d[2][s], d[3][s]);
-    v.z = pack_bf16x2(d[4][s], d[5][s]);
-    v.w = pack_bf16x2(d[6][s], d[7][s]);
+    v.x = pack_bf16x2(digit(y[0], ng[0], s), digit(y[1], ng[1], s));
+    v.y = pack_bf16x2(digit(y[2], ng[2], s), digit(y[3], ng[3], s));
+    v.z = pack_bf16x2(digit(y[4], ng[4], s), digit(y[5], ng[5], s));
+    v.w = pack_bf16x2(digit(y[6], ng[6], s), digit(y[7], ng[7], s));
     *reinterpret_cast<uint4*>(Md + ((size_t)s * npad + j) * npad + kg * 8) = v;
   }
 }
 
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+__global__ void __launch_bounds__(OZ_THREADS, 2)
     k_oz_rotate(const double* __restrict__ V, int64_t ldv, int64_t D, int n, int npad, int upper,
                 const int* er, const __nv_bfloat16* __restrict__ Md, const int* em,
                 double* __restrict__ Out, int64_t ldo) {
@@ -309,13 +324,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int64_t r0 = (int64_t)blockIdx.x * TB;
   const int j0 = blockIdx.y * TB;
   const int kend = upper ? min(npad, j0 + TB) : npad;  // M upper triangular: rows k <= j
-  __int128 acc[4][4];
+  Acc acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-  for (int kb = 0; kb < kend; kb += TB) {
-    for (int item = threadIdx.x; item < TB * 8; item += OZ_THREADS) {
+    for (int b = 0; b < 4; ++b) acc[a][b] = Acc{0, 0};
+  for (int kb = 0; kb < kend; kb += KC) {
+    for (int item = threadIdx.x; item < TB * (KC / 8); item += OZ_THREADS) {
       const int r = item % TB, kg = item / TB;
       const int64_t gr = r0 + r;
       double x[8];
@@ -326,9 +341,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       store_digits8(As + kg * 8, r, x, gr < D ? er[gr] : 0);
     }
-    for (int item = threadIdx.x; item < OZ_S * TB * 8; item += OZ_THREADS) {
-      const int s = item / (TB * 8), rem = item % (TB * 8);
-      const int c = rem / 8, kg = rem % 8;
+    for (int item = threadIdx.x; item < OZ_S * TB * (KC / 8); item += OZ_THREADS) {
+      const int s = item / (TB * (KC / 8)), rem = item % (TB * (KC / 8));
+      const int c = rem / (KC / 8), kg = rem % (KC / 8);
       *reinterpret_cast<uint4*>(Bs + ((size_t)s * TB + c) * SK + kg * 8) =
           *reinterpret_cast<const uint4*>(Md + ((size_t)s * npad + j0 + c) * npad + kb + kg * 8);
     }
@@ -339,7 +354,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   for_each_out(acc, [&](int i, int j, double v) {
     const int64_t gr = r0 + i;
     const int gj = j0 + j;
-    if (gr < D && gj < n) Out[gr * ldo + gj] = ldexp(v, er[gr] + em[gj] - 63);
+    if (gr < D && gj < n) Out[gr * ldo + gj] = ldexp(v, er[gr] + em[gj] - 64);
   });
 }
 
@@ -390,9 +405,10 @@ fd_status oz_gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, in
   if (hbad) return FD_OK;  // non-finite input: the FP64 path propagates it
   const int nti = (int)cdiv(m, TB), ntj = (int)cdiv(n, TB);
   const int tiles = sym ? nti * (nti + 1) / 2 : nti * ntj;
-  int64_t slices = std::max<int64_t>(1, cdiv(2LL * ctx->num_sms, tiles));
-  slices = std::min<int64_t>(slices, std::max<int64_t>(1, cdiv(D, 4 * TB)));
-  const int64_t rps = cdiv(cdiv(D, slices), TB) * TB;
+  int64_t slices = std::max<int64_t>(1, cdiv(4LL * ctx->num_sms, tiles));
+  slices = std::min<int64_t>(slices, std::max<int64_t>(1, cdiv(D, 4 * KC)));
+  slices = std::max<int64_t>(slices, cdiv(D, OZ_MAX_CHUNKS * KC));  // exact 64-bit accumulation
+  const int64_t rps = cdiv(cdiv(D, slices), KC) * KC;
   slices = std::max<int64_t>(1, cdiv(D, rps));
   FD_TRY(workspace(ctx, "oz_gram_partial", sizeof(double) * slices * m * n, &p));
   double* P = (double*)p;
