@@ -303,6 +303,9 @@ typedef struct {
  * converge.  The per-instance intervals and degrees follow fd_solve's
  * heuristic.  Matrices must be built with sigma = 1; N_s per instance (opt->ns
  * or nb ceil(4 n_target / nb)) must be at most 96; nb in {2, ..., 64}.
+ * A graph cannot be captured on the legacy default stream: on a context
+ * without a stream the solve runs on a private stream of its own, created for
+ * the call and ordered after the work already queued on the legacy stream.
  *   res         n_inst results
  *   theta/resid HOST arrays holding sum(n_target) doubles, instance after
  *               instance, ascending theta within an instance (NaN/inf for an

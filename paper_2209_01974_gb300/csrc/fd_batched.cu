@@ -684,6 +684,34 @@ fd_status enqueue_iteration(fd_ctx* ctx, Batch& B) {
   return FD_OK;
 }
 
+// A CUDA graph cannot be captured on the legacy default stream.  On a context
+// without a stream of its own the batched solve runs on a private stream that
+// first waits for the work already queued on the legacy stream; the caller's
+// stream is restored (and the private stream drained) on every exit.
+struct PrivateStream {
+  fd_ctx* ctx;
+  cudaStream_t saved;
+  cudaStream_t own = nullptr;
+  explicit PrivateStream(fd_ctx* c) : ctx(c), saved(c->stream) {}
+  fd_status open() {
+    if (saved != nullptr) return FD_OK;
+    FD_CUDA(ctx, cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    cudaEvent_t ev;
+    FD_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    FD_CUDA(ctx, cudaEventRecord(ev, nullptr));
+    FD_CUDA(ctx, cudaStreamWaitEvent(own, ev, 0));
+    FD_CUDA(ctx, cudaEventDestroy(ev));
+    ctx->stream = own;
+    return FD_OK;
+  }
+  ~PrivateStream() {
+    if (!own) return;
+    cudaStreamSynchronize(own);
+    ctx->stream = saved;
+    cudaStreamDestroy(own);
+  }
+};
+
 std::vector<int> nearest(const double* th, int ns, double tau) {
   std::vector<int> o(ns);
   std::iota(o.begin(), o.end(), 0);
@@ -726,6 +754,8 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
                      BMAX_NS);
   }
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  PrivateStream pstream(ctx);
+  FD_TRY(pstream.open());
   const int max_outer = opt.max_outer > 0 ? opt.max_outer : 60;
   const int n_max = opt.n_max > 0 ? opt.n_max : 100000;
   const int lsteps = opt.lanczos_steps > 0 ? opt.lanczos_steps : 20;
