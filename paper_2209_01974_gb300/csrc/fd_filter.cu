@@ -27,8 +27,15 @@ using namespace step;
 
 template <typename T, int NB, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64)
-    k_cheb_step(SellArgs<T> A, StepArgs<T> s) {
+    k_cheb_step(SellArgs<T> A, StepArgs<T> s, unsigned pf) {
   using L = Layout<T, NB>;
+  // L2 prefetch for the CTA that starts one resident wave (pf CTAs) later:
+  // its first loads (row-wise operands, then the SELL slab they index) are a
+  // chain of dependent DRAM round trips that no register budget can overlap.
+  if (pf > 0 && blockIdx.x + pf < gridDim.x) {
+    const int64_t r0 = (int64_t)(blockIdx.x + pf) * (WARPS * L::RPW);
+    prefetch_rows<T, NB, MODE>(A, s, r0, r0 + WARPS * L::RPW < A.D ? r0 + WARPS * L::RPW : A.D);
+  }
   const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
   const int64_t row0 = warp * L::RPW;
   if (row0 >= A.D) return;
@@ -57,9 +64,11 @@ fd_status launch_step(fd_ctx* ctx, const fd_matrix* M, int mode, const StepArgs<
   if constexpr (sizeof(T) == 8) A.val = (const T*)M->val; else A.val = (const T*)M->val32;
   const int64_t rows_per_block = (int64_t)WARPS * L::RPW;
   const unsigned grid = (unsigned)cdiv(M->D, rows_per_block);
-  if (mode == MODE_SPMMV) k_cheb_step<T, NB, MODE_SPMMV><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s);
-  else if (mode == MODE_SECOND) k_cheb_step<T, NB, MODE_SECOND><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s);
-  else k_cheb_step<T, NB, MODE_GENERIC><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s);
+  // prefetch distance: one wave of resident CTAs (the launch-bounds occupancy)
+  const unsigned pf = (unsigned)ctx->num_sms * (sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64);
+  if (mode == MODE_SPMMV) k_cheb_step<T, NB, MODE_SPMMV><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s, pf);
+  else if (mode == MODE_SECOND) k_cheb_step<T, NB, MODE_SECOND><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s, pf);
+  else k_cheb_step<T, NB, MODE_GENERIC><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s, pf);
   FD_LAUNCHED(ctx);
   return FD_OK;
 }

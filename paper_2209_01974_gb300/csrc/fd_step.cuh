@@ -169,6 +169,41 @@ __device__ __forceinline__ void row_product(const SellArgs<T>& A, const T* __res
   }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+
+// L2 prefetch for the rows [r0, r1) of a later CTA: the 128-byte lines of
+// their row-wise operands (the own row of X, Z, Vin) and the SELL slabs of the
+// chunks that start inside the range.  A prefetch holds no register and no
+// scoreboard entry, so the later CTA finds its first, dependent loads in L2.
+template <typename T, int NB, int MODE>
+__device__ __forceinline__ void prefetch_rows(const SellArgs<T>& A, const StepArgs<T>& s,
+                                              int64_t r0, int64_t r1) {
+  constexpr int LPR = (NB * (int)sizeof(T) + 127) / 128;  // lines per vector row
+  constexpr int NS = MODE == MODE_GENERIC ? 3 : MODE == MODE_SECOND ? 2 : 1;
+  const int n = (int)(r1 - r0) * LPR;
+  for (int q = threadIdx.x; q < NS * n; q += blockDim.x) {
+    const int st = q / n, rq = q % n;
+    const int64_t row = r0 + rq / LPR;
+    const int64_t off = (int64_t)(rq % LPR) * (128 / (int)sizeof(T));
+    const T* p = st == 0 ? s.X + row * s.ldx : st == 1 ? s.Z + row * s.ldz : s.Vin + row * s.ldvi;
+    prefetch_l2(p + off);
+  }
+  if (threadIdx.x >= blockDim.x - 32) {
+    const int64_t c0 = (r0 + A.C - 1) / A.C, c1 = (r1 + A.C - 1) / A.C;
+    if (c0 >= c1) return;
+    const int64_t e0 = A.chunk_ptr[c0], e1 = A.chunk_ptr[c1];
+    const int64_t l0c = (e0 * 4) >> 7, l1c = (e1 * 4 + 127) >> 7;
+    const int64_t l0v = (e0 * (int64_t)sizeof(T)) >> 7, l1v = (e1 * (int64_t)sizeof(T) + 127) >> 7;
+    const int64_t nc = l1c - l0c, nv = l1v - l0v;
+    const char* cb = reinterpret_cast<const char*>(A.col);
+    const char* vb = reinterpret_cast<const char*>(A.val);
+    for (int64_t q = threadIdx.x & 31; q < nc + nv; q += 32)
+      prefetch_l2(q < nc ? cb + ((l0c + q) << 7) : vb + ((l0v + q - nc) << 7));
+  }
+}
+
 // One fused Chebyshev step (or a plain SpMMV) for the warp's rows row0 ..
 // row0 + RPW - 1 (row0 < D, a multiple of RPW); all 32 lanes must call it.
 template <typename T, int NB, int MODE>
