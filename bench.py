@@ -49,8 +49,10 @@ WORKLOAD = {"workload": "anderson3d L=128 (2,097,152 rows) stencil, nb=64, degre
 
 # GB300 FP64 peak (nominal 1.25 TFLOP/s; an FMA-loop probe on this machine measured 1.20)
 FP64_TFLOPS = 1.25
-# DRAM bytes (read + write) of one generic FP32 step from ncu, profiles/ (None if stale)
-TRAFFIC_F32 = None
+# DRAM bytes (read + write) of one generic FP32 step of this workload, from one ncu
+# capture of `bench.py --kernel-only f32` (profiles/k_cheb_step_f32_stencil_L128_nb64.md);
+# set to None whenever the step kernel changes
+TRAFFIC_F32 = 1.762288e9 + 1.027285e9
 
 
 def filter_bytes(D, nnz, nb, n, Sx):
