@@ -1,4 +1,4 @@
-"""FP64 Gram and rotation products on bf16 tensor cores (Ozaki splitting) against
+"""FP64 Gram and rotation products on the tcgen05 tensor cores (Ozaki splitting) against
 FP64 references, and the CholQR / Rayleigh-Ritz steps built on them."""
 import numpy as np
 import pytest
@@ -37,8 +37,9 @@ def _block(D, n, seed, spread=6):
 
 
 def _bound(X, Y):
-    # split error <= K * 2^-56 * (4 |X|max |Y|max) per entry, the reference's own
-    # rounding <= K u sum |x||y| <= K u |X|max |Y|max: both under 8 K u |X|max |Y|max
+    # split error per term < (2^-55 truncation + 2^-53.2 dropped digit pairs) 2^(e+f)
+    # <= 2^-50.9 |X|max |Y|max, the reference's own rounding <= K u |X|max |Y|max:
+    # together under 8 K u |X|max |Y|max = K 2^-50 |X|max |Y|max
     K = X.shape[0]
     return 8 * K * U * np.outer(np.abs(X).max(0), np.abs(Y).max(0))
 
