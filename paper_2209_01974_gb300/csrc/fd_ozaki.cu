@@ -18,18 +18,22 @@
 // digit pairs; over a K chunk of 128 every partial sum stays below
 // 8 * 128 * 127^2 < 2^24, so the FP32 accumulation of the tensor core is exact.
 //
-// Kernel shape (one CTA per SM, 512 threads): a 128 x 64 output tile; the 8
-// level accumulators live in TMEM (8 x 64 FP32 columns = all 512 columns).
-// The K range runs in sub-chunks of 32: all threads cut the FP64 inputs of a
-// sub-chunk into digit slices in shared memory (two buffers, the canonical
-// no-swizzle K-major layout of 8-row x 16-byte core matrices), one thread
-// issues the 36 pairs x 2 tcgen05.mma (M 128, N 64, K 16) of the sub-chunk and
-// commits them to the buffer's mbarrier, and the next sub-chunk's digits are
-// cut while the tensor core works.  Every fourth sub-chunk (K = 128) the
-// levels are read back with tcgen05.ld, converted to integers and added,
-// scaled by 2^(7 (7 - l)), into two 64-bit integer accumulators per output
-// (levels 0-3 and 4-7; value = hi 2^28 + lo), exact for up to 2^16 chunks per
-// CTA; one conversion to FP64 at the end.
+// Two kernels per product.  A streaming kernel cuts each FP64 operand once
+// into its 8 bf16 digit slices and writes them to HBM already in the tensor
+// core's shared-memory layout (canonical no-swizzle K-major core matrices,
+// one contiguous 2 or 4 KB block per 16-deep K step, slice and 64- or
+// 128-wide operand block).  The product kernel (one CTA per SM, 512 threads,
+// a 128 x 64 output tile, the 8 level accumulators in TMEM: 8 x 64 FP32
+// columns = all 512) is a pure Blackwell pipeline: one thread streams the
+// digit blocks of each K step into a four-stage shared-memory ring with
+// cp.async.bulk (mbarrier complete_tx), one thread issues the step's 36
+// tcgen05.mma (one per digit pair; M 128, N 64, K 16) and commits them to the
+// stage's "empty" mbarrier, and every eighth step (K = 128) all threads read
+// the levels back with tcgen05.ld, convert them to 32-bit integers, combine
+// adjacent levels exactly in 32 bits and add them, scaled by 2^(7 (7 - l)),
+// into two 64-bit integer accumulators per output (levels 0-3 and 4-7; value
+// = hi 2^28 + lo), exact for up to 2^16 chunks per CTA; one conversion to FP64
+// at the end.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -46,17 +50,21 @@ constexpr int OZ_B = 7;             // bits per digit
 constexpr int OZ_F = OZ_S * OZ_B;   // 56 fraction bits
 constexpr int TM = 128;             // output tile rows (tcgen05 M)
 constexpr int TN = 64;              // output tile columns (tcgen05 N)
-constexpr int KS = 32;              // K sub-chunk (digits cut per step)
-constexpr int SUBS = 4;             // sub-chunks per exact FP32 chunk (K = 128)
+constexpr int KS = 16;              // K step (one tcgen05.mma)
+constexpr int SUBS = 8;             // K steps per exact FP32 chunk (K = 128)
+constexpr int NST = 4;              // shared-memory ring stages
 constexpr int OZ_THREADS = 512;
-constexpr int A_SLICE = TM * KS * 2;                  // 8192 bytes per digit slice
-constexpr int B_SLICE = TN * KS * 2;                  // 4096 bytes
-constexpr int BUF = OZ_S * (A_SLICE + B_SLICE);       // 98,304 bytes per buffer
+constexpr int A_SLICE = TM * KS * 2;                  // 4096 bytes per digit block
+constexpr int B_SLICE = TN * KS * 2;                  // 2048 bytes
+constexpr int A_ELEMS = A_SLICE / 2, B_ELEMS = B_SLICE / 2;
+constexpr int STAGE = OZ_S * (A_SLICE + B_SLICE);     // 49,152 bytes
 constexpr int CM_K = 128;                             // K-adjacent core matrices (LBO)
-constexpr int CM_MN = (KS / 8) * 128;                 // MN-adjacent 8-row groups (SBO) = 512
-constexpr size_t OZ_SMEM = 2 * (size_t)BUF + 64;      // + 2 mbarriers and the TMEM address
+constexpr int CM_MN = (KS / 8) * 128;                 // MN-adjacent 8-row groups (SBO) = 256
+constexpr size_t OZ_SMEM = (size_t)NST * STAGE + 2 * NST * 8 + 16;  // + barriers, TMEM address
 constexpr int64_t OZ_MAX_CHUNKS = 1 << 16;            // per CTA, keeps the accumulators exact
 constexpr unsigned TMEM_COLS = 512;                   // 8 levels x 64 columns
+constexpr int P_THREAD = 0;                           // bulk-copy producer (warp 0)
+constexpr int M_THREAD = 32;                          // MMA issuer (warp 1)
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
 // A and B bf16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4
@@ -77,7 +85,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 
 // bounded wait for the completion of the barrier phase with the given parity
@@ -102,8 +109,18 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// bulk (TMA engine) copy of `bytes` contiguous bytes, completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -147,10 +164,11 @@ __device__ __forceinline__ uint32_t bf16_of_digit(uint32_t v) {
   return __float_as_uint(__uint_as_float(0x4B000000u | v) - 8388608.0f) >> 16;
 }
 
-// the 8 digit slices of 8 consecutive K values (k group kg) of one operand
-// row, stored as one 16-byte core-matrix row per slice
-__device__ __forceinline__ void store_digits8(unsigned char* slice0, int slice_bytes, int row, int kg,
-                                              const double (&x)[8], int e) {
+// the 8 digit slices of 8 consecutive K values of one operand row (or
+// column): slice s of the 8 values is one 16-byte core-matrix row, handed to
+// put(s, v)
+template <typename Put>
+__device__ __forceinline__ void cut8(const double (&x)[8], int e, Put&& put) {
   unsigned long long y[8];
   uint32_t sg[8];
 #pragma unroll
@@ -158,7 +176,6 @@ __device__ __forceinline__ void store_digits8(unsigned char* slice0, int slice_b
   uint32_t smask[4];
 #pragma unroll
   for (int p = 0; p < 4; ++p) smask[p] = (sg[2 * p] << 15) | (sg[2 * p + 1] << 31);
-  const int off = (row >> 3) * CM_MN + kg * CM_K + (row & 7) * 16;
 #pragma unroll
   for (int s = 0; s < OZ_S; ++s) {
     const int sh = OZ_F - OZ_B * (s + 1);
@@ -169,8 +186,14 @@ __device__ __forceinline__ void store_digits8(unsigned char* slice0, int slice_b
       const uint32_t hi = bf16_of_digit((uint32_t)(y[2 * p + 1] >> sh) & 0x7Fu);
       w[p] = (lo | (hi << 16)) | smask[p];
     }
-    *reinterpret_cast<uint4*>(slice0 + (size_t)s * slice_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
+    put(s, make_uint4(w[0], w[1], w[2], w[3]));
   }
+}
+
+// byte offset of (row, k) inside one digit block: 8-row x 16-byte core
+// matrices, K-adjacent ones 128 bytes apart, row groups 256 bytes apart
+__device__ __forceinline__ int core_offset(int row, int k) {
+  return (row >> 3) * CM_MN + (k >> 3) * CM_K + (row & 7) * 16 + (k & 7) * 2;
 }
 
 // Exact accumulator of one output: value = hi 2^28 + lo in units of
@@ -198,46 +221,69 @@ __device__ __forceinline__ void issue_subchunk(uint32_t tmem, uint32_t a0, uint3
 
 // Read the 8 levels of this thread's 16 outputs (TMEM lane = tile row
 // 32 (warp & 3) + lane, columns 16 (warp >> 2) ..) into the accumulators.
+// Level sums are integers below 2^24 (l + 1 pairs x 128 x 127^2), so two
+// adjacent levels combine exactly in 32 bits (c_l 2^7 + c_{l+1} < 2^31) and
+// only 32-bit conversions are needed (64-bit ones run on GB300's slow FP64
+// units).
 __device__ __forceinline__ void flush(uint32_t tmem, Acc (&acc)[16]) {
   const int w = threadIdx.x >> 5;
   const uint32_t base = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(16 * (w >> 2));
 #pragma unroll 1
-  for (int l = 0; l < OZ_S; ++l) {
-    uint32_t r[16];
-    tmem_ld16(base + (uint32_t)(l * TN), r);
-    const long long wgt = 1ll << (l < 4 ? 7 * (3 - l) : 7 * (7 - l));
+  for (int pr = 0; pr < OZ_S / 2; ++pr) {  // level pairs (0,1) (2,3) (4,5) (6,7)
+    uint32_t r0[16], r1[16];
+    tmem_ld16(base + (uint32_t)(2 * pr * TN), r0);
+    tmem_ld16(base + (uint32_t)((2 * pr + 1) * TN), r1);
+    const int sh = (pr & 1) ? 0 : 14;  // pairs (0,1), (4,5) carry 2^14 within hi / lo
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const long long v = __float2ll_rz(__uint_as_float(r[c])) * wgt;
-      if (l < 4) acc[c].hi += v;
-      else acc[c].lo += v;
+      const int v = __float2int_rz(__uint_as_float(r0[c])) * 128 + __float2int_rz(__uint_as_float(r1[c]));
+      const long long t = (long long)v * (1LL << sh);
+      if (pr < 2) acc[c].hi += t;
+      else acc[c].lo += t;
     }
   }
 }
 
-// The pipeline shared by the Gram and rotation kernels.  `cut(sc, buf)` writes
-// the digits of sub-chunk sc into buffer buf (all threads).  Returns false if
+// The product pipeline of one CTA.  K step sc reads digit block (sc, s) of A
+// at A + sc a_kc + s a_s and of B likewise (bf16 elements).  Returns false if
 // a bounded wait gave up (the same answer in every thread).
-template <typename Cut>
-__device__ __forceinline__ bool run_tile(unsigned char* smem, uint64_t* bar, uint32_t tmem, int nsub,
-                                         Acc (&acc)[16], Cut&& cut) {
+__device__ __forceinline__ bool run_tile(unsigned char* smem, uint64_t* full, uint64_t* empty, uint32_t tmem,
+                                         const __nv_bfloat16* A, int64_t a_kc, int64_t a_s,
+                                         const __nv_bfloat16* B, int64_t b_kc, int64_t b_s, int nsub,
+                                         Acc (&acc)[16]) {
+  auto load = [&](int sc) {
+    const int st = sc % NST;
+    unsigned char* dst = smem + (size_t)st * STAGE;
+    mbar_expect_tx(&full[st], STAGE);
+#pragma unroll 1
+    for (int s = 0; s < OZ_S; ++s) {
+      bulk_g2s(dst + s * A_SLICE, A + sc * a_kc + s * a_s, A_SLICE, &full[st]);
+      bulk_g2s(dst + OZ_S * A_SLICE + s * B_SLICE, B + sc * b_kc + s * b_s, B_SLICE, &full[st]);
+    }
+  };
   bool ok = true;
+  if (threadIdx.x == P_THREAD)
+    for (int sc = 0; sc < nsub && sc < NST; ++sc) load(sc);
   for (int sc = 0; sc < nsub; ++sc) {
-    const int b = sc & 1;
-    // buffer b is free once the MMAs of sub-chunk sc - 2 have completed
-    if (sc >= 2) ok = mbar_wait(&bar[b], (uint32_t)((sc - 2) >> 1) & 1u);
-    if (__syncthreads_or(!ok)) return false;
-    cut(sc, smem + (size_t)b * BUF);
-    fence_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(smem + (size_t)b * BUF);
-      issue_subchunk(tmem, a0, a0 + OZ_S * A_SLICE, (sc % SUBS) == 0);
-      umma_commit(&bar[b]);
+    const int st = sc % NST;
+    const uint32_t par = (uint32_t)(sc / NST) & 1u;
+    if (threadIdx.x == M_THREAD && ok) {
+      ok = mbar_wait(&full[st], par);
+      if (ok) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + (size_t)st * STAGE);
+        issue_subchunk(tmem, a0, a0 + OZ_S * A_SLICE, (sc % SUBS) == 0);
+        umma_commit(&empty[st]);
+      }
+    }
+    if (threadIdx.x == P_THREAD && ok && sc + NST < nsub) {
+      // the stage is free again once the MMAs of K step sc have completed
+      ok = mbar_wait(&empty[st], par);
+      if (ok) load(sc + NST);
     }
     if ((sc % SUBS) == SUBS - 1 || sc == nsub - 1) {
-      ok = mbar_wait(&bar[b], (uint32_t)(sc >> 1) & 1u);
+      // the issuer observes the completion; the others sleep in the barrier
+      if (threadIdx.x == M_THREAD && ok) ok = mbar_wait(&empty[st], par);
       if (__syncthreads_or(!ok)) return false;
       tc_fence_after();
       flush(tmem, acc);
@@ -248,22 +294,33 @@ __device__ __forceinline__ bool run_tile(unsigned char* smem, uint64_t* bar, uin
   return true;
 }
 
-__device__ __forceinline__ double acc_value(const Acc& a) {
-  return fma((double)a.hi, 0x1.0p28, (double)a.lo);
+// hi 2^28 + lo scaled by 2^sc: one rounding in the FMA, then the scale by
+// exponent arithmetic (ldexp only where the result leaves the normal range)
+__device__ __forceinline__ double acc_value(const Acc& a, int sc) {
+  const double v = fma((double)a.hi, 0x1.0p28, (double)a.lo);
+  const long long bits = __double_as_longlong(v);
+  const int ev = (int)((bits >> 52) & 0x7FF);
+  if (v == 0.0 || ev + sc <= 0 || ev + sc >= 2047) return ldexp(v, sc);
+  return __longlong_as_double(bits + (long long)sc * (1LL << 52));
 }
 
-// CTA prologue: TMEM (warp 0) and the two mbarriers
-__device__ __forceinline__ uint32_t tile_setup(unsigned char* smem, uint64_t** bar) {
-  *bar = reinterpret_cast<uint64_t*>(smem + 2 * (size_t)BUF);
-  uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 2 * (size_t)BUF + 16);
+// CTA prologue: TMEM (warp 0) and the full / empty mbarriers of the ring
+__device__ __forceinline__ uint32_t tile_setup(unsigned char* smem, uint64_t** full, uint64_t** empty) {
+  unsigned char* tail = smem + (size_t)NST * STAGE;
+  *full = reinterpret_cast<uint64_t*>(tail);
+  *empty = *full + NST;
+  uint32_t* holder = reinterpret_cast<uint32_t*>(tail + 2 * NST * 8);
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(holder)),
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (threadIdx.x == 32) {
-    mbar_init(&(*bar)[0]);
-    mbar_init(&(*bar)[1]);
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(&(*full)[i]);
+      mbar_init(&(*empty)[i]);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
@@ -280,16 +337,18 @@ __device__ __forceinline__ void tile_teardown(uint32_t tmem) {
   }
 }
 
-// Stage the tile's 16 outputs per thread through shared memory (the digit
-// buffers are free once the last flush is done) and hand every output to
-// `put(i, j, v)` with consecutive threads on consecutive columns.
-template <typename Put>
-__device__ __forceinline__ void write_tile(unsigned char* smem, const Acc (&acc)[16], Put&& put) {
+// Hand every output of the tile to put(i, j, v): the thread owning it
+// converts (scale(i, j) gives the power of two), then the values are staged
+// through shared memory (free once the last flush is done) so that the
+// stores run with consecutive threads on consecutive columns.
+template <typename Scale, typename Put>
+__device__ __forceinline__ void write_tile(unsigned char* smem, const Acc (&acc)[16], Scale&& scale,
+                                           Put&& put) {
   double* st = reinterpret_cast<double*>(smem);  // [TM][TN + 1]
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (w & 3) + lane, col0 = 16 * (w >> 2);
 #pragma unroll
-  for (int c = 0; c < 16; ++c) st[row * (TN + 1) + col0 + c] = acc_value(acc[c]);
+  for (int c = 0; c < 16; ++c) st[row * (TN + 1) + col0 + c] = acc_value(acc[c], scale(row, col0 + c));
   __syncthreads();
   for (int e = threadIdx.x; e < TM * TN; e += OZ_THREADS) {
     const int i = e / TN, j = e % TN;
@@ -341,13 +400,68 @@ __global__ void k_row_exp(const double* V, int64_t ld, int64_t D, int n, int* ex
 }
 
 // ---------------------------------------------------------------------------
-// Gram: P[slice][i][j] = sum over the slice's rows k of X[k][i] Y[k][j];
+// digit blocks in HBM
+//   column-scaled operand (Gram X or Y, rotation M), w columns over K rows:
+//     block (kc, s, cb) of 64 columns x 16 k at ((kc * 8 + s) * ncb + cb) * 1024,
+//     so a 128-column A tile is two adjacent blocks (4 KB)
+//   row-scaled operand (rotation V), D rows over K = n columns:
+//     block (rb, kc, s) of 128 rows x 16 k at ((rb * nkc + kc) * 8 + s) * 2048
+// ---------------------------------------------------------------------------
+__global__ void k_digits_cols(const double* __restrict__ X, int64_t ld, int64_t D, int w, int wpad,
+                              const int* ex, int64_t nkc, __nv_bfloat16* __restrict__ Xd) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= nkc * 2 * wpad) return;
+  const int c = (int)(item % wpad);
+  const int64_t g = item / wpad;  // group of 8 consecutive k
+  const int64_t k0 = 8 * g, kc = g >> 1;
+  double x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = (c < w && k0 + q < D) ? X[(k0 + q) * ld + c] : 0.0;
+  const int ncb = wpad / 64;
+  unsigned char* blk = reinterpret_cast<unsigned char*>(Xd + (kc * 8 * ncb + (c >> 6)) * B_ELEMS);
+  const int off = core_offset(c & 63, (int)(k0 & 15));
+  cut8(x, c < w ? ex[c] : 0, [&](int s, uint4 v) {
+    *reinterpret_cast<uint4*>(blk + (size_t)s * ncb * B_SLICE + off) = v;
+  });
+}
+
+__global__ void k_digits_rows(const double* __restrict__ V, int64_t ldv, int64_t D, int n, int64_t Dpad,
+                              int npad, const int* er, int vec, __nv_bfloat16* __restrict__ Vd) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int groups = npad / 8;
+  if (item >= Dpad * groups) return;
+  const int g = (int)(item % groups);  // consecutive threads: consecutive k of one row
+  const int64_t r = item / groups;
+  const int k0 = 8 * g;
+  double x[8];
+  if (vec && r < D && k0 + 8 <= n) {  // 16-byte aligned rows: four 16-byte loads
+    const double2* p = reinterpret_cast<const double2*>(V + r * ldv + k0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double2 t = __ldg(p + q);
+      x[2 * q] = t.x;
+      x[2 * q + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = (r < D && k0 + q < n) ? V[r * ldv + k0 + q] : 0.0;
+  }
+  const int64_t nkc = npad / KS;
+  unsigned char* blk = reinterpret_cast<unsigned char*>(Vd + ((r >> 7) * nkc + (k0 >> 4)) * 8 * A_ELEMS);
+  const int off = core_offset((int)(r & 127), k0 & 15);
+  cut8(x, r < D ? er[r] : 0, [&](int s, uint4 v) {
+    *reinterpret_cast<uint4*>(blk + (size_t)s * A_SLICE + off) = v;
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Gram: P[slice][i][j] = sum over the slice's K steps of X[k][i] Y[k][j];
 // tile (ti, tj) covers i in [128 ti, +128), j in [64 tj, +64); for a symmetric
 // product only the tiles that reach the upper triangle (tj >= 2 ti) run
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_gram(const double* __restrict__ X, int64_t ldx, const double* __restrict__ Y, int64_t ldy,
-              int64_t D, int m, int n, int ntj, int sym, int64_t rows_per_slice, const int* ex,
+    k_oz_gram(const __nv_bfloat16* __restrict__ Xd, int ncbx, const __nv_bfloat16* __restrict__ Yd, int ncby,
+              int64_t nkc, int m, int n, int ntj, int sym, int64_t kc_per_slice, const int* ex,
               const int* ey, double* __restrict__ P, int* err) {
   extern __shared__ __align__(128) unsigned char smem[];
   int t = blockIdx.x, ti = 0, tj;
@@ -364,45 +478,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     tj = t % ntj;
   }
   const int i0 = ti * TM, j0 = tj * TN;
-  const int64_t k0 = (int64_t)blockIdx.y * rows_per_slice;
-  const int64_t k1 = min(D, k0 + rows_per_slice);
-  uint64_t* bar;
-  const uint32_t tmem = tile_setup(smem, &bar);
+  const int64_t kc0 = (int64_t)blockIdx.y * kc_per_slice;
+  const int nsub = (int)min(kc_per_slice, nkc - kc0);
+  uint64_t *full, *empty;
+  const uint32_t tmem = tile_setup(smem, &full, &empty);
   Acc acc[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) acc[c] = Acc{0, 0};
-  const int nsub = (int)((k1 - k0 + KS - 1) / KS);
-  // digit work items: A (X columns i0 ..) 128 x 4, then B (Y columns j0 ..) 64 x 4
-  auto cut = [&](int sc, unsigned char* buf) {
-    const int64_t kb = k0 + (int64_t)sc * KS;
-    for (int item = threadIdx.x; item < (TM + TN) * (KS / 8); item += OZ_THREADS) {
-      const bool isA = item < TM * (KS / 8);
-      const int it = isA ? item : item - TM * (KS / 8);
-      const int rows = isA ? TM : TN;
-      const int c = it % rows, kg = it / rows;
-      const int col = (isA ? i0 : j0) + c;
-      const int lim = isA ? m : n;
-      const double* src = isA ? X : Y;
-      const int64_t lds = isA ? ldx : ldy;
-      double x[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int64_t k = kb + kg * 8 + q;
-        x[q] = (col < lim && k < k1) ? src[k * lds + col] : 0.0;
-      }
-      const int e = col < lim ? (isA ? ex[col] : ey[col]) : 0;
-      store_digits8(buf + (isA ? 0 : OZ_S * A_SLICE), isA ? A_SLICE : B_SLICE, c, kg, x, e);
-    }
-  };
-  const bool ok = run_tile(smem, bar, tmem, nsub, acc, cut);
+  const int64_t a_kc = 8LL * ncbx * B_ELEMS, a_s = (int64_t)ncbx * B_ELEMS;
+  const int64_t b_kc = 8LL * ncby * B_ELEMS, b_s = (int64_t)ncby * B_ELEMS;
+  const bool ok = run_tile(smem, full, empty, tmem, Xd + kc0 * a_kc + (int64_t)(2 * ti) * B_ELEMS, a_kc, a_s,
+                           Yd + kc0 * b_kc + (int64_t)tj * B_ELEMS, b_kc, b_s, nsub, acc);
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(err, 1);
   } else {
     double* Ps = P + (int64_t)blockIdx.y * m * n;
-    write_tile(smem, acc, [&](int i, int j, double v) {
-      const int gi = i0 + i, gj = j0 + j;
-      if (gi < m && gj < n) Ps[(int64_t)gi * n + gj] = ldexp(v, ex[gi] + ey[gj] - 63);
-    });
+    write_tile(
+        smem, acc,
+        [&](int i, int j) {
+          const int gi = i0 + i, gj = j0 + j;
+          return (gi < m && gj < n) ? ex[gi] + ey[gj] - 63 : 0;
+        },
+        [&](int i, int j, double v) {
+          const int gi = i0 + i, gj = j0 + j;
+          if (gi < m && gj < n) Ps[(int64_t)gi * n + gj] = v;
+        });
   }
   tile_teardown(tmem);
 }
@@ -420,86 +520,43 @@ __global__ void k_oz_gram_reduce(const double* P, int slices, int m, int n, int 
 }
 
 // ---------------------------------------------------------------------------
-// rotation: Out[r][j] = sum_k V[r][k] M[k][j]; the digits of M are computed
-// once (k_m_digits) as Md[t][j][k] (npad x npad per slice) with column
-// exponents em[j]
+// rotation: Out[r][j] = sum_k V[r][k] M[k][j] from the row-scaled digits of V
+// and the column-scaled digits of M; tile (rb, jt) covers rows [128 rb, +128)
+// and columns [64 jt, +64)
 // ---------------------------------------------------------------------------
-__global__ void k_m_digits(const double* M, int n, int npad, const int* em, __nv_bfloat16* Md) {
-  // one thread per (j, 8 consecutive k)
-  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int groups = npad / 8;
-  if (item >= (int64_t)npad * groups) return;
-  const int j = (int)(item / groups), kg = (int)(item % groups);
-  double x[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int k = kg * 8 + q;
-    x[q] = (j < n && k < n) ? M[(int64_t)k * n + j] : 0.0;
-  }
-  const int e = j < n ? em[j] : 0;
-  unsigned long long y[8];
-  uint32_t sg[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) y[q] = fixed56(x[q], e, &sg[q]);
-#pragma unroll
-  for (int s = 0; s < OZ_S; ++s) {
-    const int sh = OZ_F - OZ_B * (s + 1);
-    uint32_t w[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const uint32_t lo = bf16_of_digit((uint32_t)(y[2 * p] >> sh) & 0x7Fu) | (sg[2 * p] << 15);
-      const uint32_t hi = bf16_of_digit((uint32_t)(y[2 * p + 1] >> sh) & 0x7Fu) | (sg[2 * p + 1] << 15);
-      w[p] = lo | (hi << 16);
-    }
-    *reinterpret_cast<uint4*>(Md + ((size_t)s * npad + j) * npad + kg * 8) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_rotate(const double* __restrict__ V, int64_t ldv, int64_t D, int n, int npad, int upper,
-                const int* er, const __nv_bfloat16* __restrict__ Md, const int* em,
+    k_oz_rotate(const __nv_bfloat16* __restrict__ Vd, const __nv_bfloat16* __restrict__ Md, int ncbm,
+                int64_t D, int n, int npad, int upper, const int* er, const int* em,
                 double* __restrict__ Out, int64_t ldo, int* err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int64_t r0 = (int64_t)blockIdx.x * TM;
-  const int j0 = blockIdx.y * TN;
+  const int64_t rb = blockIdx.x;
+  const int jt = blockIdx.y, j0 = jt * TN;
   const int kend = upper ? min(npad, j0 + TN) : npad;  // M upper triangular: rows k <= j
-  uint64_t* bar;
-  const uint32_t tmem = tile_setup(smem, &bar);
+  const int64_t nkc = npad / KS;
+  uint64_t *full, *empty;
+  const uint32_t tmem = tile_setup(smem, &full, &empty);
   Acc acc[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) acc[c] = Acc{0, 0};
-  const int nsub = (kend + KS - 1) / KS;
-  auto cut = [&](int sc, unsigned char* buf) {
-    const int kb = sc * KS;
-    {  // A: rows of V, one (row, 8 consecutive k) item per thread
-      const int r = threadIdx.x % TM, kg = threadIdx.x / TM;
-      const int64_t gr = r0 + r;
-      double x[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = kb + kg * 8 + q;
-        x[q] = (gr < D && k < n) ? V[gr * ldv + k] : 0.0;
-      }
-      store_digits8(buf, A_SLICE, r, kg, x, gr < D ? er[gr] : 0);
-    }
-    // B: the precomputed digits of M, 16 bytes per (slice, column, k group)
-    unsigned char* bb = buf + OZ_S * A_SLICE;
-    for (int item = threadIdx.x; item < OZ_S * TN * (KS / 8); item += OZ_THREADS) {
-      const int s = item / (TN * (KS / 8)), rem = item % (TN * (KS / 8));
-      const int c = rem / (KS / 8), kg = rem % (KS / 8);
-      *reinterpret_cast<uint4*>(bb + (size_t)s * B_SLICE + (c >> 3) * CM_MN + kg * CM_K + (c & 7) * 16) =
-          *reinterpret_cast<const uint4*>(Md + ((size_t)s * npad + j0 + c) * npad + kb + kg * 8);
-    }
-  };
-  const bool ok = run_tile(smem, bar, tmem, nsub, acc, cut);
+  const int64_t b_kc = 8LL * ncbm * B_ELEMS, b_s = (int64_t)ncbm * B_ELEMS;
+  const bool ok = run_tile(smem, full, empty, tmem, Vd + rb * nkc * 8 * A_ELEMS, 8LL * A_ELEMS, A_ELEMS,
+                           Md + (int64_t)jt * B_ELEMS, b_kc, b_s, kend / KS, acc);
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(err, 1);
   } else {
-    write_tile(smem, acc, [&](int i, int j, double v) {
-      const int64_t gr = r0 + i;
-      const int gj = j0 + j;
-      if (gr < D && gj < n) Out[gr * ldo + gj] = ldexp(v, er[gr] + em[gj] - 63);
-    });
+    const int64_t r0 = rb * TM;
+    write_tile(
+        smem, acc,
+        [&](int i, int j) {
+          const int64_t gr = r0 + i;
+          const int gj = j0 + j;
+          return (gr < D && gj < n) ? er[gr] + em[gj] - 63 : 0;
+        },
+        [&](int i, int j, double v) {
+          const int64_t gr = r0 + i;
+          const int gj = j0 + j;
+          if (gr < D && gj < n) Out[gr * ldo + gj] = v;
+        });
   }
   tile_teardown(tmem);
 }
@@ -523,6 +580,28 @@ fd_status check_wait_flag(fd_ctx* ctx, const int* flag) {
   return FD_OK;
 }
 
+// digit workspace; false (no error) if it cannot be allocated: the caller
+// then takes the FP64 path
+bool digit_workspace(fd_ctx* ctx, const char* name, size_t bytes, __nv_bfloat16** out) {
+  void* p = nullptr;
+  if (workspace(ctx, name, bytes, &p) != FD_OK) {
+    ctx->err.clear();
+    return false;
+  }
+  *out = (__nv_bfloat16*)p;
+  return true;
+}
+
+// column-scaled digits of a D x w operand (K = D rows, padded to 16)
+fd_status cut_cols(fd_ctx* ctx, const double* X, int64_t ld, int64_t D, int w, const int* ex,
+                   __nv_bfloat16* Xd, int64_t nkc) {
+  const int wpad = (int)cdiv(w, TM) * TM;
+  const int64_t items = nkc * 2 * wpad;
+  k_digits_cols<<<(unsigned)cdiv(items, 256), 256, 0, ctx->stream>>>(X, ld, D, w, wpad, ex, nkc, Xd);
+  FD_LAUNCHED(ctx);
+  return FD_OK;
+}
+
 }  // namespace
 
 // Column exponents of X (n columns over D rows); non-finite values raise *bad.
@@ -542,6 +621,16 @@ fd_status oz_gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, in
                   int m, int n, double* C, int ldc, bool sym, bool* used) {
   *used = false;
   FD_TRY(set_attrs(ctx));
+  const bool same = Y == X && ldy == ldx;
+  const int64_t nkc = cdiv(D, KS);
+  const int ncbx = (int)cdiv(m, TM) * 2, ncby = (int)cdiv(n, TM) * 2;
+  __nv_bfloat16 *Xd, *Yd;
+  if (!digit_workspace(ctx, "oz_digits_a", sizeof(__nv_bfloat16) * (size_t)nkc * KS * ncbx * 64 * OZ_S, &Xd))
+    return FD_OK;
+  Yd = Xd;
+  if (!same &&
+      !digit_workspace(ctx, "oz_digits_b", sizeof(__nv_bfloat16) * (size_t)nkc * KS * ncby * 64 * OZ_S, &Yd))
+    return FD_OK;
   void* p;
   FD_TRY(workspace(ctx, "oz_exp", sizeof(int) * ((size_t)m + n + 8), &p));
   int* ex = (int*)p;
@@ -550,12 +639,14 @@ fd_status oz_gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, in
   int* err = bad + 1;
   FD_CUDA(ctx, cudaMemsetAsync(bad, 0, 2 * sizeof(int), ctx->stream));
   FD_TRY(col_exponents(ctx, X, ldx, D, m, ex, bad));
-  if (Y != X || ldy != ldx) FD_TRY(col_exponents(ctx, Y, ldy, D, n, ey, bad));
+  if (!same) FD_TRY(col_exponents(ctx, Y, ldy, D, n, ey, bad));
   else FD_CUDA(ctx, cudaMemcpyAsync(ey, ex, sizeof(int) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   int hbad = 0;
   FD_CUDA(ctx, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   FD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (hbad) return FD_OK;  // non-finite input: the FP64 path propagates it
+  FD_TRY(cut_cols(ctx, X, ldx, D, m, ex, Xd, nkc));
+  if (!same) FD_TRY(cut_cols(ctx, Y, ldy, D, n, ey, Yd, nkc));
   const int nti = (int)cdiv(m, TM), ntj = (int)cdiv(n, TN);
   int tiles = 0;
   if (sym) {
@@ -563,16 +654,16 @@ fd_status oz_gram(fd_ctx* ctx, const double* X, int64_t ldx, const double* Y, in
   } else {
     tiles = nti * ntj;
   }
-  // about four waves of one CTA per SM, K slices in whole 128-row chunks
+  // about four waves of one CTA per SM; at most 2^16 exact chunks per CTA
   int64_t slices = std::max<int64_t>(1, (4LL * ctx->num_sms) / tiles);
-  slices = std::min<int64_t>(slices, std::max<int64_t>(1, cdiv(D, 4 * SUBS * KS)));
-  slices = std::max<int64_t>(slices, cdiv(D, OZ_MAX_CHUNKS * SUBS * KS));
-  const int64_t rps = cdiv(cdiv(D, slices), SUBS * KS) * (SUBS * KS);
-  slices = std::max<int64_t>(1, cdiv(D, rps));
+  slices = std::min<int64_t>(slices, std::max<int64_t>(1, cdiv(nkc, 4 * SUBS)));
+  slices = std::max<int64_t>(slices, cdiv(nkc, OZ_MAX_CHUNKS * SUBS));
+  const int64_t kps = cdiv(nkc, slices);
+  slices = cdiv(nkc, kps);
   FD_TRY(workspace(ctx, "oz_gram_partial", sizeof(double) * slices * m * n, &p));
   double* P = (double*)p;
   k_oz_gram<<<dim3(tiles, (unsigned)slices), OZ_THREADS, OZ_SMEM, ctx->stream>>>(
-      X, ldx, Y, ldy, D, m, n, ntj, sym ? 1 : 0, rps, ex, ey, P, err);
+      Xd, ncbx, Yd, ncby, nkc, m, n, ntj, sym ? 1 : 0, kps, ex, ey, P, err);
   FD_LAUNCHED(ctx);
   FD_TRY(check_wait_flag(ctx, err));
   k_oz_gram_reduce<<<(unsigned)cdiv((int64_t)m * n, 256), 256, 0, ctx->stream>>>(P, (int)slices, m, n,
@@ -586,12 +677,17 @@ fd_status oz_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const
                     bool* used) {
   *used = false;
   FD_TRY(set_attrs(ctx));
-  const int npad = (int)cdiv(n, TN) * TN;
+  const int npad = (int)cdiv(n, TN) * TN;  // K of the product, in whole 64-column blocks of M
+  const int64_t Dpad = cdiv(D, TM) * TM;
+  const int ncbm = (int)cdiv(n, TM) * 2;
+  __nv_bfloat16 *Vd, *Md;
+  if (!digit_workspace(ctx, "oz_digits_a", sizeof(__nv_bfloat16) * (size_t)Dpad * npad * OZ_S, &Vd))
+    return FD_OK;
+  if (!digit_workspace(ctx, "oz_digits_m", sizeof(__nv_bfloat16) * (size_t)npad * ncbm * 64 * OZ_S, &Md))
+    return FD_OK;
   void* p;
-  FD_TRY(workspace(ctx, "oz_rot_small", sizeof(int) * ((size_t)n + D + 8) +
-                                            sizeof(__nv_bfloat16) * (size_t)OZ_S * npad * npad + 256, &p));
-  __nv_bfloat16* Md = (__nv_bfloat16*)p;
-  int* em = (int*)(Md + (size_t)OZ_S * npad * npad);
+  FD_TRY(workspace(ctx, "oz_rot_small", sizeof(int) * ((size_t)n + D + 8), &p));
+  int* em = (int*)p;
   int* er = em + n;
   int* bad = er + D;
   int* err = bad + 1;
@@ -603,13 +699,15 @@ fd_status oz_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const
   FD_CUDA(ctx, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   FD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (hbad) return FD_OK;
-  const int groups = npad / 8;
-  k_m_digits<<<(unsigned)cdiv((int64_t)npad * groups, 256), 256, 0, ctx->stream>>>(M, n, npad, em, Md);
+  FD_TRY(cut_cols(ctx, M, n, n, n, em, Md, npad / KS));
+  const int64_t items = Dpad * (npad / 8);
+  const int vec = (((uintptr_t)V & 15) == 0 && (ldv & 1) == 0) ? 1 : 0;
+  k_digits_rows<<<(unsigned)cdiv(items, 256), 256, 0, ctx->stream>>>(V, ldv, D, n, Dpad, npad, er, vec, Vd);
   FD_LAUNCHED(ctx);
   FD_TRY(workspace(ctx, "oz_rot_out", sizeof(double) * (size_t)D * n, &p));
   double* Out = (double*)p;
-  k_oz_rotate<<<dim3((unsigned)cdiv(D, TM), (unsigned)(npad / TN)), OZ_THREADS, OZ_SMEM, ctx->stream>>>(
-      V, ldv, D, n, npad, upper ? 1 : 0, er, Md, em, Out, n, err);
+  k_oz_rotate<<<dim3((unsigned)(Dpad / TM), (unsigned)(npad / TN)), OZ_THREADS, OZ_SMEM, ctx->stream>>>(
+      Vd, Md, ncbm, D, n, npad, upper ? 1 : 0, er, em, Out, n, err);
   FD_LAUNCHED(ctx);
   FD_TRY(check_wait_flag(ctx, err));
   FD_CUDA(ctx, cudaMemcpy2DAsync(V, ldv * sizeof(double), Out, n * sizeof(double), n * sizeof(double), D,
