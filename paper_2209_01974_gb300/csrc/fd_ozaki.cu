@@ -63,7 +63,7 @@ constexpr int CM_MN = (KS / 8) * 128;                 // MN-adjacent 8-row group
 constexpr size_t OZ_SMEM = (size_t)NST * STAGE + 2 * NST * 8 + 16;  // + barriers, TMEM address
 constexpr int64_t OZ_MAX_CHUNKS = 1 << 16;            // per CTA, keeps the accumulators exact
 constexpr unsigned TMEM_COLS = 512;                   // 8 levels x 64 columns
-constexpr int P_THREAD = 0;                           // bulk-copy producer (warp 0)
+constexpr int P_THREAD = 0;                           // bulk-copy producer (warp 0, lanes 0-15)
 constexpr int M_THREAD = 32;                          // MMA issuer (warp 1)
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
@@ -202,21 +202,19 @@ struct Acc {
   long long hi, lo;
 };
 
-// One sub-chunk's tensor-core work (issued by one thread): level l collects
-// the pairs (s, l - s) in its TMEM columns l * 64 ..; the first MMA of a level
-// in a K chunk overwrites, the rest accumulate.
-__device__ __forceinline__ void issue_subchunk(uint32_t tmem, uint32_t a0, uint32_t b0, bool first) {
-#pragma unroll 1
-  for (int l = 0; l < OZ_S; ++l) {
-#pragma unroll 1
-    for (int s = 0; s <= l; ++s) {
-      const uint32_t a = a0 + (uint32_t)(s * A_SLICE), b = b0 + (uint32_t)((l - s) * B_SLICE);
+// One K step's tensor-core work (issued by one thread): level l collects the
+// pairs (s, l - s) in its TMEM columns l * 64 ..; the first MMA of a level in
+// a K chunk overwrites, the rest accumulate.  Fully unrolled: the descriptor
+// of slice s is the base descriptor plus s * slice bytes / 16 in its address
+// field, an immediate.
+template <bool FIRST>
+__device__ __forceinline__ void issue_step(uint32_t tmem, uint64_t adesc, uint64_t bdesc) {
 #pragma unroll
-      for (int ks = 0; ks < KS / 16; ++ks)
-        umma(tmem + (uint32_t)(l * TN), sdesc(a + ks * 2 * CM_K), sdesc(b + ks * 2 * CM_K),
-             (first && s == 0 && ks == 0) ? 0u : 1u);
-    }
-  }
+  for (int l = 0; l < OZ_S; ++l)
+#pragma unroll
+    for (int s = 0; s <= l; ++s)
+      umma(tmem + (uint32_t)(l * TN), adesc + (uint64_t)((s * A_SLICE) >> 4),
+           bdesc + (uint64_t)(((l - s) * B_SLICE) >> 4), (FIRST && s == 0) ? 0u : 1u);
 }
 
 // Read the 8 levels of this thread's 16 outputs (TMEM lane = tile row
@@ -251,18 +249,24 @@ __device__ __forceinline__ bool run_tile(unsigned char* smem, uint64_t* full, ui
                                          const __nv_bfloat16* A, int64_t a_kc, int64_t a_s,
                                          const __nv_bfloat16* B, int64_t b_kc, int64_t b_s, int nsub,
                                          Acc (&acc)[16]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // producer warp: lane 0 posts the stage's byte count, lanes 0-15 issue one
+  // bulk copy each (slice lane / 2 of A or B)
   auto load = [&](int sc) {
     const int st = sc % NST;
     unsigned char* dst = smem + (size_t)st * STAGE;
-    mbar_expect_tx(&full[st], STAGE);
-#pragma unroll 1
-    for (int s = 0; s < OZ_S; ++s) {
-      bulk_g2s(dst + s * A_SLICE, A + sc * a_kc + s * a_s, A_SLICE, &full[st]);
-      bulk_g2s(dst + OZ_S * A_SLICE + s * B_SLICE, B + sc * b_kc + s * b_s, B_SLICE, &full[st]);
+    if (lane == 0) mbar_expect_tx(&full[st], STAGE);
+    __syncwarp();
+    if (lane < 2 * OZ_S) {
+      const int s = lane >> 1;
+      if (lane & 1)
+        bulk_g2s(dst + OZ_S * A_SLICE + s * B_SLICE, B + sc * b_kc + s * b_s, B_SLICE, &full[st]);
+      else
+        bulk_g2s(dst + s * A_SLICE, A + sc * a_kc + s * a_s, A_SLICE, &full[st]);
     }
   };
   bool ok = true;
-  if (threadIdx.x == P_THREAD)
+  if (warp == P_THREAD / 32)
     for (int sc = 0; sc < nsub && sc < NST; ++sc) load(sc);
   for (int sc = 0; sc < nsub; ++sc) {
     const int st = sc % NST;
@@ -272,11 +276,13 @@ __device__ __forceinline__ bool run_tile(unsigned char* smem, uint64_t* full, ui
       if (ok) {
         tc_fence_after();
         const uint32_t a0 = smem_u32(smem + (size_t)st * STAGE);
-        issue_subchunk(tmem, a0, a0 + OZ_S * A_SLICE, (sc % SUBS) == 0);
+        const uint64_t ad = sdesc(a0), bd = sdesc(a0 + OZ_S * A_SLICE);
+        if ((sc % SUBS) == 0) issue_step<true>(tmem, ad, bd);
+        else issue_step<false>(tmem, ad, bd);
         umma_commit(&empty[st]);
       }
     }
-    if (threadIdx.x == P_THREAD && ok && sc + NST < nsub) {
+    if (warp == P_THREAD / 32 && ok && sc + NST < nsub) {
       // the stage is free again once the MMAs of K step sc have completed
       ok = mbar_wait(&empty[st], par);
       if (ok) load(sc + NST);
@@ -294,14 +300,52 @@ __device__ __forceinline__ bool run_tile(unsigned char* smem, uint64_t* full, ui
   return true;
 }
 
-// hi 2^28 + lo scaled by 2^sc: one rounding in the FMA, then the scale by
-// exponent arithmetic (ldexp only where the result leaves the normal range)
+// hi 2^28 + lo scaled by 2^sc, rounded once to nearest (ties to even) by
+// integer arithmetic: int64 -> FP64 conversions and FP64 arithmetic run on
+// GB300's slow FP64 units
 __device__ __forceinline__ double acc_value(const Acc& a, int sc) {
-  const double v = fma((double)a.hi, 0x1.0p28, (double)a.lo);
-  const long long bits = __double_as_longlong(v);
-  const int ev = (int)((bits >> 52) & 0x7FF);
-  if (v == 0.0 || ev + sc <= 0 || ev + sc >= 2047) return ldexp(v, sc);
-  return __longlong_as_double(bits + (long long)sc * (1LL << 52));
+  // 128-bit two's complement N = hi 2^28 + lo as (H, L)
+  unsigned long long L = (unsigned long long)a.hi << 28;
+  long long H = a.hi >> 36;
+  const unsigned long long lo = (unsigned long long)a.lo;
+  const unsigned long long L2 = L + lo;
+  H += (a.lo >> 63) + (L2 < L ? 1 : 0);  // sign extension of lo, carry
+  L = L2;
+  const bool neg = H < 0;
+  unsigned long long mh = (unsigned long long)H, ml = L;
+  if (neg) {  // magnitude
+    ml = ~ml + 1;
+    mh = ~mh + (ml == 0 ? 1 : 0);
+  }
+  if (mh == 0 && ml == 0) return 0.0;
+  const int p = mh ? 127 - __clzll((long long)mh) : 63 - __clzll((long long)ml);  // leading bit
+  unsigned long long m;  // 53-bit significand
+  if (p <= 52) {
+    m = ml << (52 - p);
+  } else {
+    const int sh = p - 52;  // 1 .. 75
+    unsigned long long q, rem_hi, rem_lo;  // q = N >> sh; remainder bits below
+    if (sh < 64) {
+      q = (ml >> sh) | (mh << (64 - sh));
+      rem_hi = (ml >> (sh - 1)) & 1u;
+      rem_lo = sh > 1 ? (ml & ((1ull << (sh - 1)) - 1)) : 0;
+    } else {
+      q = mh >> (sh - 64);
+      rem_hi = sh == 64 ? (ml >> 63) : ((mh >> (sh - 65)) & 1u);
+      rem_lo = sh == 64 ? (ml & ~(1ull << 63)) : ((mh & ((1ull << (sh - 65)) - 1)) | ml);
+    }
+    m = q;
+    if (rem_hi && (rem_lo || (m & 1u))) ++m;
+  }
+  int e = p + sc;  // value = m 2^(e - 52)
+  if (m >> 53) {
+    m >>= 1;
+    ++e;
+  }
+  if (e < -1022 || e > 1023) return ldexp(neg ? -(double)m : (double)m, e - 52);
+  const unsigned long long bits = ((unsigned long long)(neg ? 1 : 0) << 63) |
+                                  ((unsigned long long)(e + 1023) << 52) | (m & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
 }
 
 // CTA prologue: TMEM (warp 0) and the full / empty mbarriers of the ring
@@ -529,8 +573,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 int64_t D, int n, int npad, int upper, const int* er, const int* em,
                 double* __restrict__ Out, int64_t ldo, int* err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int64_t rb = blockIdx.x;
-  const int jt = blockIdx.y, j0 = jt * TN;
+  // the column tiles of one row block are consecutive CTAs, so the row
+  // block's digits are read from HBM once and then from L2
+  const int njt = npad / TN;
+  const int64_t rb = blockIdx.x / njt;
+  const int jt = (int)(blockIdx.x % njt), j0 = jt * TN;
   const int kend = upper ? min(npad, j0 + TN) : npad;  // M upper triangular: rows k <= j
   const int64_t nkc = npad / KS;
   uint64_t *full, *empty;
@@ -706,7 +753,7 @@ fd_status oz_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const
   FD_LAUNCHED(ctx);
   FD_TRY(workspace(ctx, "oz_rot_out", sizeof(double) * (size_t)D * n, &p));
   double* Out = (double*)p;
-  k_oz_rotate<<<dim3((unsigned)(Dpad / TM), (unsigned)(npad / TN)), OZ_THREADS, OZ_SMEM, ctx->stream>>>(
+  k_oz_rotate<<<(unsigned)((Dpad / TM) * (npad / TN)), OZ_THREADS, OZ_SMEM, ctx->stream>>>(
       Vd, Md, ncbm, D, n, npad, upper ? 1 : 0, er, em, Out, n, err);
   FD_LAUNCHED(ctx);
   FD_TRY(check_wait_flag(ctx, err));
