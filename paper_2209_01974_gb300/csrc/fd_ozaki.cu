@@ -424,24 +424,6 @@ __global__ void k_col_exp(const double* part, int nb, int n, int* ex) {
   if (m > 0.0) frexp(m, &e);
   ex[c] = e;
 }
-__global__ void k_row_exp(const double* V, int64_t ld, int64_t D, int n, int* ex, int* bad) {
-  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (r >= D) return;
-  double m = 0.0;
-  for (int c = lane; c < n; c += 32) {
-    const double v = fabs(V[r * ld + c]);
-    if (!(v <= 1.0e300)) *bad = 1;
-    m = fmax(m, v);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) {
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);
-    ex[r] = e;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // digit blocks in HBM
@@ -469,33 +451,47 @@ __global__ void k_digits_cols(const double* __restrict__ X, int64_t ld, int64_t 
   });
 }
 
+// one warp per row: the row's exponent (max |v| over the row, written to
+// er[r]; a non-finite value raises *bad), then its digit blocks
 __global__ void k_digits_rows(const double* __restrict__ V, int64_t ldv, int64_t D, int n, int64_t Dpad,
-                              int npad, const int* er, int vec, __nv_bfloat16* __restrict__ Vd) {
-  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int groups = npad / 8;
-  if (item >= Dpad * groups) return;
-  const int g = (int)(item % groups);  // consecutive threads: consecutive k of one row
-  const int64_t r = item / groups;
-  const int k0 = 8 * g;
-  double x[8];
-  if (vec && r < D && k0 + 8 <= n) {  // 16-byte aligned rows: four 16-byte loads
-    const double2* p = reinterpret_cast<const double2*>(V + r * ldv + k0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const double2 t = __ldg(p + q);
-      x[2 * q] = t.x;
-      x[2 * q + 1] = t.y;
+                              int npad, int vec, int* er, int* bad, __nv_bfloat16* __restrict__ Vd) {
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= Dpad) return;
+  const bool live = r < D;
+  const double* row = V + r * ldv;
+  double m = 0.0;
+  if (live)
+    for (int c = lane; c < n; c += 32) {
+      const double v = fabs(row[c]);
+      if (!(v <= 1.0e300)) *bad = 1;  // NaN or inf
+      m = fmax(m, v);
     }
-  } else {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = (r < D && k0 + q < n) ? V[r * ldv + k0 + q] : 0.0;
-  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  if (live && lane == 0) er[r] = e;
   const int64_t nkc = npad / KS;
-  unsigned char* blk = reinterpret_cast<unsigned char*>(Vd + ((r >> 7) * nkc + (k0 >> 4)) * 8 * A_ELEMS);
-  const int off = core_offset((int)(r & 127), k0 & 15);
-  cut8(x, r < D ? er[r] : 0, [&](int s, uint4 v) {
-    *reinterpret_cast<uint4*>(blk + (size_t)s * A_SLICE + off) = v;
-  });
+  for (int g = lane; g < npad / 8; g += 32) {  // groups of 8 consecutive k (L1-resident row)
+    const int k0 = 8 * g;
+    double x[8];
+    if (vec && live && k0 + 8 <= n) {  // 16-byte aligned rows: four 16-byte loads
+      const double2* p = reinterpret_cast<const double2*>(row + k0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double2 t = __ldg(p + q);
+        x[2 * q] = t.x;
+        x[2 * q + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = (live && k0 + q < n) ? row[k0 + q] : 0.0;
+    }
+    unsigned char* blk = reinterpret_cast<unsigned char*>(Vd + ((r >> 7) * nkc + (k0 >> 4)) * 8 * A_ELEMS);
+    const int off = core_offset((int)(r & 127), k0 & 15);
+    cut8(x, e, [&](int s, uint4 v) { *reinterpret_cast<uint4*>(blk + (size_t)s * A_SLICE + off) = v; });
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -740,17 +736,14 @@ fd_status oz_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const
   int* err = bad + 1;
   FD_CUDA(ctx, cudaMemsetAsync(bad, 0, 2 * sizeof(int), ctx->stream));
   FD_TRY(col_exponents(ctx, M, n, n, n, em, bad));
-  k_row_exp<<<(unsigned)cdiv(D, 8), 256, 0, ctx->stream>>>(V, ldv, D, n, er, bad);
+  FD_TRY(cut_cols(ctx, M, n, n, n, em, Md, npad / KS));
+  const int vec = (((uintptr_t)V & 15) == 0 && (ldv & 1) == 0) ? 1 : 0;
+  k_digits_rows<<<(unsigned)cdiv(Dpad, 8), 256, 0, ctx->stream>>>(V, ldv, D, n, Dpad, npad, vec, er, bad, Vd);
   FD_LAUNCHED(ctx);
   int hbad = 0;
   FD_CUDA(ctx, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   FD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (hbad) return FD_OK;
-  FD_TRY(cut_cols(ctx, M, n, n, n, em, Md, npad / KS));
-  const int64_t items = Dpad * (npad / 8);
-  const int vec = (((uintptr_t)V & 15) == 0 && (ldv & 1) == 0) ? 1 : 0;
-  k_digits_rows<<<(unsigned)cdiv(items, 256), 256, 0, ctx->stream>>>(V, ldv, D, n, Dpad, npad, er, vec, Vd);
-  FD_LAUNCHED(ctx);
+  if (hbad) return FD_OK;  // non-finite input: the FP64 path propagates it
   FD_TRY(workspace(ctx, "oz_rot_out", sizeof(double) * (size_t)D * n, &p));
   double* Out = (double*)p;
   k_oz_rotate<<<(unsigned)((Dpad / TM) * (npad / TN)), OZ_THREADS, OZ_SMEM, ctx->stream>>>(
