@@ -496,6 +496,36 @@ def run_learned_eval(args):
     return 0
 
 
+def run_tts(args):
+    """Time to N_t eigenpairs at residual <= 1e-9 on a mid-size matrix, for the
+    three forms: plain FP64 (heuristic interval and degree), FP32 sweeps with an
+    FP64 finish (heuristic), and FP32 sweeps with the trained filter-parameter
+    predictor.  Each form's eigenvalues are compared with the FP64 form's."""
+    import paper_2209_01974_gb300 as fd
+    from paper_2209_01974_gb300 import predictor
+    ctx = fd.fd_create(0)
+    A = fd.fd_build_matrix(ctx, args.tts_spec)
+    a, b = -args.tts_half_width, args.tts_half_width
+    nt, nb = args.tts_nt, args.nb if args.nb != NB else 32
+    params = predictor.load()
+    out = {}
+    ref = None
+    for name, prec, p in (("f64", "f64", None), ("f32", "f32", None), ("f32_learned", "f32", params)):
+        th, rho, res, pred = predictor.solve_with(ctx, p, A, a, b, nt, nb, 100, 1e-9, seed=0, precision=prec,
+                                                  max_outer=args.max_outer, n_max=args.n_max)
+        if ref is None:
+            ref = np.sort(th)
+        out[name] = {"converged": res["converged"], "seconds": res["t_total"],
+                     "iterations": res["iterations"], "n_spmmv": res["n_spmmv"],
+                     "n_spmmv_f32": res["n_spmmv_f32"], "final_degree": res["final_degree"],
+                     "max_resid": float(rho.max()),
+                     "max_abs_dtheta_vs_f64": float(np.abs(np.sort(th) - ref).max()),
+                     "params": pred}
+    print(json.dumps({"tts_workload": f"{args.tts_spec} ({A.D} rows), {nt} eigenpairs nearest the "
+                                      f"centre of [{a}, {b}], nb={nb}, degree >= 100, tol 1e-9", **out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,7 +545,14 @@ def main():
     ap.add_argument("--learned-eval", action="store_true",
                     help="predictor vs heuristic on the road-like graph Laplacian")
     ap.add_argument("--side", type=int, default=400)
+    ap.add_argument("--tts", action="store_true",
+                    help="time to solution of the FP64, FP32 and learned forms on a mid-size matrix")
+    ap.add_argument("--tts-spec", default="anderson3d:L=48,W=16,seed=3")
+    ap.add_argument("--tts-nt", type=int, default=32)
+    ap.add_argument("--tts-half-width", type=float, default=0.002)
     args = ap.parse_args()
+    if args.tts:
+        return run_tts(args)
     if args.learned_eval:
         return run_learned_eval(args)
     if args.batched:

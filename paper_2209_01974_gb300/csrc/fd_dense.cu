@@ -177,6 +177,53 @@ __global__ void __launch_bounds__(1024) k_cholesky(const double* G, int n, doubl
   if (threadIdx.x == 0) *ok = fail ? 0 : 1;
 }
 
+// Cooperative version (one CTA per SM): the same right-looking elimination,
+// each step's trailing update spread over the CTAs by rows, one grid barrier
+// per column.  Row k is read unscaled during step k (the update uses
+// R_kj R_ki / d) and scaled by its owner after the barrier, when no CTA reads it
+// any more.  Reads of R bypass L1 (other CTAs wrote them).
+__global__ void __launch_bounds__(256) k_cholesky_coop(const double* G, int n, double coeff, double* R,
+                                                       int* ok) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[256];
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tr += G[(int64_t)i * n + i];
+  red[threadIdx.x] = tr;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double shift = coeff * red[0];
+  for (int i = blockIdx.x; i < n; i += gridDim.x)
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      R[(int64_t)i * n + j] = j >= i ? G[(int64_t)i * n + j] + (i == j ? shift : 0.0) : 0.0;
+  grid.sync();
+  bool fail = false;
+  for (int k = 0; k < n; ++k) {
+    const double d = __ldcg(R + (int64_t)k * n + k);
+    if (!(d > 0.0) || !isfinite(d)) {  // the same value in every CTA: all stop here
+      fail = true;
+      break;
+    }
+    const double inv = 1.0 / d;
+    const double* rk = R + (int64_t)k * n;
+    for (int i = k + 1 + blockIdx.x; i < n; i += gridDim.x) {
+      const double a = __ldcg(rk + i) * inv;
+      double* ri = R + (int64_t)i * n;
+      for (int j = i + threadIdx.x; j < n; j += blockDim.x) ri[j] -= a * __ldcg(rk + j);
+    }
+    grid.sync();
+    if (k % gridDim.x == blockIdx.x) {
+      const double r = sqrt(d), rinv = 1.0 / r;
+      double* rw = R + (int64_t)k * n;
+      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) rw[j] *= rinv;
+      if (threadIdx.x == 0) rw[k] = r;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ok = fail ? 0 : 1;
+}
+
 // ---------------------------------------------------------------------------
 // triangular inverse: X = R^-1 (upper), one warp per column
 // ---------------------------------------------------------------------------
@@ -468,6 +515,20 @@ fd_status rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const do
 }
 
 fd_status cholesky(fd_ctx* ctx, const double* G, int n, double coeff, double* R, int* ok_dev) {
+  if (n >= 64) {  // one CTA per SM, co-resident (cooperative launch)
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cholesky_coop, 256, 0);
+    if (per_sm >= 1) {
+      const int grid = std::min(ctx->num_sms, n);
+      void* args[] = {(void*)&G, (void*)&n, (void*)&coeff, (void*)&R, (void*)&ok_dev};
+      if (cudaLaunchCooperativeKernel((const void*)k_cholesky_coop, grid, 256, args, 0, ctx->stream) ==
+          cudaSuccess) {
+        ctx->launches++;
+        return FD_OK;
+      }
+      cudaGetLastError();  // cooperative launch unavailable: the one-CTA kernel below
+    }
+  }
   k_cholesky<<<1, 1024, 0, ctx->stream>>>(G, n, coeff, R, ok_dev);
   FD_LAUNCHED(ctx);
   return FD_OK;
