@@ -400,19 +400,30 @@ __device__ __forceinline__ void write_tile(unsigned char* smem, const Acc (&acc)
   }
 }
 
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
 // ---------------------------------------------------------------------------
 // scales: exponent e with max |x| < 2^e (frexp); flag non-finite input
 // ---------------------------------------------------------------------------
 __global__ void k_col_maxabs(const double* X, int64_t ld, int64_t D, int n, double* part, int* bad) {
   // grid (n_blocks_rows); each thread owns columns c = tid, tid + 256, ...
+  // maxima of |x| as 64-bit integers (the bit patterns of non-negative doubles
+  // order like their values, NaN above inf): integer instructions instead of
+  // GB300's slow FP64 ones
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    double m = 0.0;
-    for (int64_t r = blockIdx.x; r < D; r += gridDim.x) {
-      const double v = fabs(X[r * ld + c]);
-      if (!(v <= 1.0e300)) *bad = 1;  // NaN or inf
-      m = fmax(m, v);
+    unsigned long long m[4] = {0, 0, 0, 0};  // four independent loads in flight
+    const int64_t g = gridDim.x;
+    int64_t r = blockIdx.x;
+    for (; r + 3 * g < D; r += 4 * g) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m[u] = max(m[u], abs_bits(X[(r + u * g) * ld + c]));
     }
-    part[(int64_t)blockIdx.x * n + c] = m;
+    for (; r < D; r += g) m[0] = max(m[0], abs_bits(X[r * ld + c]));
+    const unsigned long long mm = max(max(m[0], m[1]), max(m[2], m[3]));
+    if (mm >= 0x7FF0000000000000ull) *bad = 1;  // NaN or inf
+    part[(int64_t)blockIdx.x * n + c] = __longlong_as_double((long long)mm);
   }
 }
 __global__ void k_col_exp(const double* part, int nb, int n, int* ex) {
@@ -460,16 +471,17 @@ __global__ void k_digits_rows(const double* __restrict__ V, int64_t ldv, int64_t
   if (r >= Dpad) return;
   const bool live = r < D;
   const double* row = V + r * ldv;
-  double m = 0.0;
+  unsigned long long mb = 0;  // max |v| as integer bits (see k_col_maxabs)
   if (live)
-    for (int c = lane; c < n; c += 32) {
-      const double v = fabs(row[c]);
-      if (!(v <= 1.0e300)) *bad = 1;  // NaN or inf
-      m = fmax(m, v);
-    }
+    for (int c = lane; c < n; c += 32) mb = max(mb, abs_bits(row[c]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if (mb >= 0x7FF0000000000000ull) {  // NaN or inf
+    if (lane == 0) *bad = 1;
+    mb = 0;
+  }
   int e = 0;
+  const double m = __longlong_as_double((long long)mb);
   if (m > 0.0) frexp(m, &e);
   if (live && lane == 0) er[r] = e;
   const int64_t nkc = npad / KS;
