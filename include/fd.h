@@ -176,12 +176,17 @@ fd_status fd_spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec,
 /* How the FP64 Gram and rotation products of fd_orthonormalize,
  * fd_rayleigh_ritz and fd_solve are computed.
  *   FD_GEMM_FP64   FP64 FMA arithmetic (GB300 runs FP64 at about 1/64 of FP32)
- *   FD_GEMM_OZAKI  exact splitting into 7-bit integer digits on bf16 tensor
- *                  cores (Ozaki scheme, 8 digits per operand relative to each
- *                  row / column maximum, 128-bit integer accumulation): FP64
- *                  accuracy at tensor-core speed
+ *   FD_GEMM_OZAKI  exact splitting into 7-bit integer digits on the tcgen05
+ *                  tensor cores (Ozaki scheme, 8 bf16 digits per operand
+ *                  relative to each row / column maximum, FP32 level sums in
+ *                  TMEM exact over K chunks of 128, 2 x 64-bit integer
+ *                  accumulation): FP64 accuracy at tensor-core speed.  Uses a
+ *                  grow-only device workspace of 16 bytes per operand element
+ *                  for the digit tiles
  *   FD_GEMM_AUTO   Ozaki for D >= 65536 and at least 64 columns, else FP64
- * Inputs holding NaN or infinity always take the FP64 path. */
+ * Inputs holding NaN or infinity always take the FP64 path, and so does a
+ * product whose digit workspace cannot be allocated.  A bounded device-side
+ * wait that gives up in a tensor-core product returns FD_ERR_TIMEOUT. */
 typedef enum { FD_GEMM_AUTO = 0, FD_GEMM_FP64 = 1, FD_GEMM_OZAKI = 2 } fd_gemm_mode;
 fd_status fd_set_gemm_mode(fd_ctx* ctx, fd_gemm_mode mode);
 
