@@ -255,7 +255,9 @@ typedef struct {
   int lanczos_steps; /* [20] */
   uint64_t seed;     /* start block: SplitMix64 stream 2 (Lanczos: stream 3) [0] */
   int precision;     /* FD_F64: all-FP64 sweeps; FD_F32: FP32 sweeps until the
-                        FP32 floor, then FP64 sweeps [FD_F64] */
+                        largest wanted residual reaches 100 u32 |H| or fails to
+                        halve in two iterations in a row, then FP64 sweeps
+                        [FD_F64] */
   double c_n;        /* degree = c_n pi / dtheta [4] */
   double m_l, m_r;   /* window edge = target edge + m (search edge - target edge) [0.5] */
   int verbose;       /* 1: print one line per outer iteration to stderr */

@@ -346,6 +346,7 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_ta
   bool use_f32 = opt.precision == FD_F32;
   std::vector<double> th(ns), rho(ns);
   double prev_max = INFINITY;
+  int stall = 0;
   int it = 0;
   bool done = false;
   for (; it < max_outer; ++it) {
@@ -370,8 +371,10 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_ta
               wl, wr, nconv, n_target, maxr, use_f32 ? "f32" : "f64");
     if (nconv == n_target) { done = true; ++it; break; }
     if (it == max_outer - 1) { ++it; break; }  // keep V = Ritz vectors of the last step
-    // precision switch: FP32 sweeps until their floor or a stall
-    if (use_f32 && (maxr <= 100.0 * 0x1.0p-24 * normH || maxr > 0.5 * prev_max)) use_f32 = false;
+    // precision switch: FP32 sweeps until their floor or a stall (two
+    // iterations in a row without halving the largest wanted residual)
+    stall = maxr > 0.5 * prev_max ? stall + 1 : 0;
+    if (use_f32 && (maxr <= 100.0 * 0x1.0p-24 * normH || stall >= 2)) use_f32 = false;
     prev_max = maxr;
     // a Ritz value outside the inclusion interval widens it
     if (th[0] < lam_l) lam_l -= 2 * widen;
