@@ -190,6 +190,15 @@ fd_status fd_spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec,
 typedef enum { FD_GEMM_AUTO = 0, FD_GEMM_FP64 = 1, FD_GEMM_OZAKI = 2 } fd_gemm_mode;
 fd_status fd_set_gemm_mode(fd_ctx* ctx, fd_gemm_mode mode);
 
+/* Diagnostic of the failure path of the tensor-core products (the paper has
+ * no counterpart): launches one CTA that initialises an mbarrier nobody
+ * arrives on and waits for it with the same bounded wait the products use,
+ * given up after `limit_us` microseconds of SM clock (1 .. 10,000,000; other
+ * values return FD_ERR_ARG).  Returns FD_ERR_TIMEOUT, with no CUDA error
+ * left behind and the context still usable; the GPU does not fault or hang.
+ * Synchronises. */
+fd_status fd_check_bounded_wait(fd_ctx* ctx, int limit_us);
+
 /* Gram product C = X^T Y (device; X: D x m with ldx, Y: D x n with ldy, C: m x n
  * row-major with ldc), the tall-skinny contraction of Cholesky-QR and
  * Rayleigh-Ritz (Sec. 2).  X == Y (same pointer and ld, m == n) computes the

@@ -75,6 +75,7 @@ _SIGS = {
     "fd_filter_coeffs": (_i32, [_dbl, _dbl, _i32, _pd]),
     "fd_spmmv": (_i32, [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _i32]),
     "fd_set_gemm_mode": (_i32, [_vp, _i32]),
+    "fd_check_bounded_wait": (_i32, [_vp, _i32]),
     "fd_gram": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _i32, _vp, _i32]),
     "fd_rotate": (_i32, [_vp, _vp, _i64, _i64, _i32, _vp, _i32]),
     "fd_copy_block": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _i64, _i64, _i32]),
@@ -279,6 +280,12 @@ def fd_set_gemm_mode(ctx, mode):
     if isinstance(mode, str):
         mode = {"auto": 0, "fp64": 1, "ozaki": 2}[mode]
     _check(ctx, _lib.fd_set_gemm_mode(ctx.handle, mode))
+
+
+def fd_check_bounded_wait(ctx, limit_us=100000):
+    """The bounded-wait diagnostic; returns its fd_status (FD_ERR_TIMEOUT when the
+    wait gave up as designed) instead of raising."""
+    return _lib.fd_check_bounded_wait(ctx.handle, int(limit_us))
 
 
 def fd_gram(ctx, X, Y):

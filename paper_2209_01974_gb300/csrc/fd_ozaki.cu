@@ -87,8 +87,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
 }
 
-// bounded wait for the completion of the barrier phase with the given parity
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait for the completion of the barrier phase with the given parity;
+// gives up after `limit` SM clock cycles (default about 2 s at 2 GHz)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = 4000000000ll) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -99,7 +100,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > 4000000000ll) return false;  // about 2 s at 2 GHz
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -616,6 +617,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   tile_teardown(tmem);
 }
 
+// the failure path in isolation: a barrier nobody arrives on
+__global__ void k_wait_unsatisfied(long long limit, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, limit);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 bool attrs_set = false;
 
 fd_status set_attrs(fd_ctx* ctx) {
@@ -769,3 +782,22 @@ fd_status oz_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const
 }
 
 }  // namespace fdi
+
+using namespace fdi;
+
+extern "C" fd_status fd_check_bounded_wait(fd_ctx* ctx, int limit_us) {
+  if (!ctx) return FD_ERR_ARG;
+  ctx->err.clear();
+  if (limit_us < 1 || limit_us > 10000000) return set_err(ctx, FD_ERR_ARG, "limit_us must be 1 .. 10^7");
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  int khz = 0;
+  FD_CUDA(ctx, cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device));
+  void* p;
+  FD_TRY(workspace(ctx, "wait_check", sizeof(int), &p));
+  int* err = (int*)p;
+  FD_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  const long long limit = (long long)limit_us * (khz > 0 ? khz : 2000000) / 1000;
+  k_wait_unsatisfied<<<1, 32, 0, ctx->stream>>>(limit, err);
+  FD_LAUNCHED(ctx);
+  return check_wait_flag(ctx, err);
+}

@@ -115,3 +115,15 @@ def test_ozaki_nonfinite_input_takes_fp64_path(fd, ctx):
     with pytest.raises(fd.FDError) as e:
         fd.fd_orthonormalize(ctx, _t(bad))
     assert e.value.status == fd.FD_ERR_BREAKDOWN
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(fd, ctx):
+    # an mbarrier nobody arrives on: the same bounded wait as the tensor-core
+    # products gives up after 0.1 s and the call reports FD_ERR_TIMEOUT
+    assert fd.fd_check_bounded_wait(ctx, 100000) == fd.FD_ERR_TIMEOUT
+    assert fd.fd_check_bounded_wait(ctx, 0) == fd.FD_ERR_ARG
+    # the context and the device still work afterwards
+    X = _block(20000, 96, 5)
+    fd.fd_set_gemm_mode(ctx, "ozaki")
+    C = fd.fd_gram(ctx, _t(X), _t(X)).cpu().numpy()
+    assert np.all(np.abs(C - X.T @ X) <= _bound(X, X))
