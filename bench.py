@@ -496,6 +496,29 @@ def run_learned_eval(args):
     return 0
 
 
+def run_chi(args):
+    """Communication metrics chi_1..3 (Sec. 3.1) of the workload matrices for
+    N_p = 2 .. 64, computed on the GPU from the sparsity pattern (Tables 2, 7)."""
+    import paper_2209_01974_gb300 as fd
+    ctx = fd.fd_create(0)
+    specs = {"Hubbard14 (Table 2)": "hubbard:n_sites=14,n_up=7,n_dn=7,t=1,U=4,bc=open",
+             "SpinChain24 pattern (Table 7)": "hubbard:n_sites=24,n_up=12,n_dn=0,t=1,U=4,bc=open",
+             "Anderson L=128 stencil": "anderson3d:L=128,W=2,seed=1",
+             "road graph 4.2M": "roadgraph:side=2048,q=0.3,seed=0"}
+    out = {}
+    for name, spec in specs.items():
+        A = fd.fd_build_matrix(ctx, spec, C=64, sigma=1)
+        rows = []
+        t0 = time.perf_counter()
+        for n_p in (2, 4, 8, 16, 32, 64):
+            c1, c2, c3, _, _ = fd.fd_comm_metrics(ctx, A, n_p)
+            rows.append({"N_p": n_p, "chi_1": round(c1, 4), "chi_2": round(c2, 4), "chi_3": round(c3, 4)})
+        out[name] = {"spec": spec, "D": A.D, "seconds_all_N_p": time.perf_counter() - t0, "rows": rows}
+        A.free()
+    print(json.dumps({"chi": out}))
+    return 0
+
+
 def run_tts(args):
     """Time to N_t eigenpairs at residual <= 1e-9 on a mid-size matrix, for the
     forms named in --tts-forms: plain FP64 (heuristic interval and degree), FP32
@@ -549,6 +572,8 @@ def main():
     ap.add_argument("--learned-eval", action="store_true",
                     help="predictor vs heuristic on the road-like graph Laplacian")
     ap.add_argument("--side", type=int, default=400)
+    ap.add_argument("--chi", action="store_true",
+                    help="communication metrics of the workload matrices (Sec. 3.1)")
     ap.add_argument("--tts", action="store_true",
                     help="time to solution of the FP64, FP32 and learned forms on a mid-size matrix")
     ap.add_argument("--tts-spec", default="anderson3d:L=48,W=16,seed=3")
@@ -556,6 +581,8 @@ def main():
     ap.add_argument("--tts-half-width", type=float, default=0.002)
     ap.add_argument("--tts-forms", default="f64,f32,f32_learned")
     args = ap.parse_args()
+    if args.chi:
+        return run_chi(args)
     if args.tts:
         return run_tts(args)
     if args.learned_eval:

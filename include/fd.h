@@ -341,6 +341,19 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
 fd_status fd_tune_batched(fd_ctx* ctx, int n_inst, const char* const* specs, int n_target,
                           int probe_degree, int* nb, int* C, int* cta_warps, double* gbs);
 
+/* Communication metrics of distributed SpMV (Sec. 3.1, Eqs. chi) for the
+ * uniform distribution of the rows over n_p processes: process p owns rows
+ * [floor(p D / n_p), floor((p + 1) D / n_p)).  Per process, the number of
+ * distinct vector entries its rows read (stored entries with a nonzero value)
+ * inside its own range (n_vm) and outside it (n_vc); and
+ *   chi[0] = chi_1 = max_p n_vc / n_vm,  chi[1] = chi_2 = sum_p n_vc / D,
+ *   chi[2] = chi_3 = n_p max_p n_vc / D   (all 0 for n_p = 1).
+ * The matrix must be in its original row order (built with sigma = 1, else
+ * FD_ERR_ARG); 1 <= n_p <= D.  n_vc, n_vm: HOST arrays of n_p int64 or NULL;
+ * chi: HOST array of 3 doubles.  Uses a D-bit device workspace.  Synchronises. */
+fd_status fd_comm_metrics(fd_ctx* ctx, const fd_matrix* A, int n_p, int64_t* n_vc,
+                          int64_t* n_vm, double* chi);
+
 /* Kernel-polynomial moments mu_m = (1/(R D)) sum_r r^T T_m(A~) r, m <
  * n_moments, with R = n_random normal-like random vectors (SplitMix64 stream
  * 4, `seed`) and A~ = alpha H + beta I (Sec. 4.1 computes the DOS with KPM).

@@ -76,6 +76,8 @@ _SIGS = {
     "fd_spmmv": (_i32, [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _i32]),
     "fd_set_gemm_mode": (_i32, [_vp, _i32]),
     "fd_check_bounded_wait": (_i32, [_vp, _i32]),
+    "fd_comm_metrics": (_i32, [_vp, _vp, _i32, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64), _pd]),
     "fd_gram": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _i32, _vp, _i32]),
     "fd_rotate": (_i32, [_vp, _vp, _i64, _i64, _i32, _vp, _i32]),
     "fd_copy_block": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _i64, _i64, _i32]),
@@ -286,6 +288,19 @@ def fd_check_bounded_wait(ctx, limit_us=100000):
     """The bounded-wait diagnostic; returns its fd_status (FD_ERR_TIMEOUT when the
     wait gave up as designed) instead of raising."""
     return _lib.fd_check_bounded_wait(ctx.handle, int(limit_us))
+
+
+def fd_comm_metrics(ctx, A, n_p):
+    """Communication metrics of distributed SpMV over n_p processes (Sec. 3.1):
+    (chi_1, chi_2, chi_3, n_vc, n_vm) with int64 arrays n_vc, n_vm per process."""
+    n_vc = np.zeros(n_p, dtype=np.int64)
+    n_vm = np.zeros(n_p, dtype=np.int64)
+    chi = np.zeros(3)
+    _check(ctx, _lib.fd_comm_metrics(ctx.handle, A.handle, int(n_p),
+                                     n_vc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     n_vm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     _dptr(chi, ctypes.c_double)))
+    return float(chi[0]), float(chi[1]), float(chi[2]), n_vc, n_vm
 
 
 def fd_gram(ctx, X, Y):
