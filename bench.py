@@ -338,6 +338,7 @@ def run_gpu(args):
 KERNEL_WORKLOADS = {
     "stencil": SPEC,
     "hubbard14": "hubbard:n_sites=14,n_up=7,n_dn=7,t=1,U=4,bc=periodic",
+    "hubbard14kron": "hubbard:n_sites=14,n_up=7,n_dn=7,t=1,U=4,bc=periodic,kron=1",
     "roadgraph": "roadgraph:side=2000,q=0.3,seed=0",
 }
 

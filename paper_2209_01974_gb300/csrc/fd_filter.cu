@@ -42,6 +42,16 @@ __global__ void __launch_bounds__(WARPS * 32, sizeof(T) == 4 ? MIN_BLOCKS : MIN_
   cheb_rows<T, NB, MODE>(A, s, row0);
 }
 
+template <typename T, int NB, int MODE>
+__global__ void __launch_bounds__(WARPS * 32, MIN_BLOCKS_F64)  // 64 registers: no spills
+    k_kron_step(KronArgs<T> K, StepArgs<T> s) {
+  using L = Layout<T, NB>;
+  const int64_t warp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+  const int64_t row0 = warp * L::RPW;
+  if (row0 >= K.D) return;
+  kron_rows<T, NB, MODE>(K, s, row0);
+}
+
 // dst[i] = src[perm[i]] (to SELL order) or dst[perm[i]] = src[i] (back)
 template <typename T>
 __global__ void k_permute_rows(const T* src, int64_t lds, T* dst, int64_t ldd,
@@ -57,7 +67,37 @@ __global__ void k_permute_rows(const T* src, int64_t lds, T* dst, int64_t ldd,
 
 // ---- dispatch -------------------------------------------------------------
 template <typename T, int NB>
+fd_status launch_kron_step(fd_ctx* ctx, const fd_matrix* M, int mode, const StepArgs<T>& s) {
+  using L = Layout<T, NB>;
+  KronArgs<T> K;
+  K.D = M->D;
+  K.dim_dn = M->kdim[1];
+  K.bits_up = M->kbits[0];
+  K.bits_dn = M->kbits[1];
+  K.ptr_up = M->kptr[0];
+  K.col_up = M->kcol[0];
+  K.ptr_dn = M->kptr[1];
+  K.col_dn = M->kcol[1];
+  if constexpr (sizeof(T) == 8) {
+    K.val_up = (const T*)M->kval[0];
+    K.val_dn = (const T*)M->kval[1];
+    K.diag = (const T*)M->kdiag;
+  } else {
+    K.val_up = (const T*)M->kval32[0];
+    K.val_dn = (const T*)M->kval32[1];
+    K.diag = (const T*)M->kdiag32;
+  }
+  const unsigned grid = (unsigned)cdiv(M->D, (int64_t)WARPS * L::RPW);
+  if (mode == MODE_SPMMV) k_kron_step<T, NB, MODE_SPMMV><<<grid, WARPS * 32, 0, ctx->stream>>>(K, s);
+  else if (mode == MODE_SECOND) k_kron_step<T, NB, MODE_SECOND><<<grid, WARPS * 32, 0, ctx->stream>>>(K, s);
+  else k_kron_step<T, NB, MODE_GENERIC><<<grid, WARPS * 32, 0, ctx->stream>>>(K, s);
+  FD_LAUNCHED(ctx);
+  return FD_OK;
+}
+
+template <typename T, int NB>
 fd_status launch_step(fd_ctx* ctx, const fd_matrix* M, int mode, const StepArgs<T>& s) {
+  if (M->kron) return launch_kron_step<T, NB>(ctx, M, mode, s);
   using L = Layout<T, NB>;
   SellArgs<T> A;
   A.chunk_ptr = M->chunk_ptr; A.row_len = M->row_len; A.col = M->col; A.D = M->D; A.C = M->C;

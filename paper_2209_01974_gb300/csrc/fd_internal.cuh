@@ -44,6 +44,19 @@ struct fd_matrix {
   int64_t* perm = nullptr;       // D: SELL row -> original row
   int64_t* iperm = nullptr;      // D: original row -> SELL row
   uint8_t* diag_added = nullptr; // D (SELL order): 1 if the diagonal was not in the input
+  // Matrix-free Hubbard operator (spec flag kron=1; rows in original order):
+  // H = H_up x 1 + 1 x H_dn + U n_double with row = rank_up * dim_dn + rank_dn.
+  // Per spin species s (0 up, 1 down): the states' bit strings and their
+  // hopping lists, targets ascending, value -t * fermion sign.
+  int kron = 0;
+  double* kdiag = nullptr;          // 25: U * n for n doubly occupied sites
+  float* kdiag32 = nullptr;         // 25: (float) (U * n)
+  int64_t kdim[2] = {0, 0};
+  uint32_t* kbits[2] = {nullptr, nullptr};
+  int64_t* kptr[2] = {nullptr, nullptr};   // kdim + 1
+  int32_t* kcol[2] = {nullptr, nullptr};
+  double* kval[2] = {nullptr, nullptr};
+  float* kval32[2] = {nullptr, nullptr};
 };
 
 namespace fdi {

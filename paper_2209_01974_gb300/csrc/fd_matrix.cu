@@ -245,6 +245,52 @@ __global__ void k_hubbard_count(HubbardP p, int64_t* cnt) {
   cnt[row] = hubbard_row(p, row, cols, vals);
 }
 
+// single-species tables of the matrix-free Hubbard operator: the hopping of
+// N particles of one spin on L sites, bonds and signs as in hubbard_row
+__device__ int kron_hops(int L, int N, int periodic, double t, int64_t r, int64_t* cols, double* vals,
+                         uint32_t* bits) {
+  const uint32_t s = comb_unrank(r, N, L);
+  *bits = s;
+  int n = 0;
+  const int nbond = L - 1 + (periodic ? 1 : 0);
+  for (int b = 0; b < nbond; ++b) {
+    const int i = b < L - 1 ? b : 0;
+    const int j = b < L - 1 ? b + 1 : L - 1;
+    if ((((s >> i) ^ (s >> j)) & 1u) == 0) continue;
+    const uint32_t between = ((1u << j) - 1u) ^ ((1u << (i + 1)) - 1u);
+    const uint32_t s2 = s ^ ((1u << i) | (1u << j));
+    cols[n] = comb_rank(s2);
+    vals[n] = -t * ((__popc(s & between) & 1) ? -1.0 : 1.0);
+    ++n;
+  }
+  return n;
+}
+
+__global__ void k_kron_count(int L, int N, int periodic, double t, int64_t dim, int64_t* cnt, uint32_t* bits) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= dim) return;
+  int64_t c[24];
+  double v[24];
+  cnt[r] = kron_hops(L, N, periodic, t, r, c, v, bits + r);
+}
+
+__global__ void k_kron_fill(int L, int N, int periodic, double t, int64_t dim, const int64_t* ptr,
+                            int32_t* col, double* val, float* val32) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= dim) return;
+  int64_t c[24];
+  double v[24];
+  uint32_t bits;
+  const int n = kron_hops(L, N, periodic, t, r, c, v, &bits);
+  sort_entries(c, v, n);
+  const int64_t o = ptr[r];
+  for (int k = 0; k < n; ++k) {
+    col[o + k] = (int32_t)c[k];
+    val[o + k] = v[k];
+    val32[o + k] = (float)v[k];
+  }
+}
+
 __global__ void k_hubbard_fill(HubbardP p, const int64_t* rowptr, int32_t* col, double* val) {
   int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= p.D) return;
@@ -727,6 +773,48 @@ const char* fd_last_error(const fd_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 int64_t fd_kernel_launches(const fd_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+// the per-species tables of the matrix-free Hubbard operator on A
+static fd_status build_kron(fd_ctx* ctx, fd_matrix* A, const HubbardP& p) {
+  cudaStream_t st = ctx->stream;
+  const int T = 256;
+  for (int sp = 0; sp < 2; ++sp) {
+    const int N = sp == 0 ? p.Nu : p.Nd;
+    const int64_t dim = sp == 0 ? p.dim_up : p.dim_dn;
+    A->kdim[sp] = dim;
+    int64_t* cnt;
+    FD_CUDA(ctx, cudaMalloc(&A->kbits[sp], sizeof(uint32_t) * dim));
+    FD_CUDA(ctx, cudaMalloc(&A->kptr[sp], sizeof(int64_t) * (dim + 1)));
+    FD_CUDA(ctx, cudaMalloc(&cnt, sizeof(int64_t) * dim));
+    k_kron_count<<<(unsigned)cdiv(dim, T), T, 0, st>>>(p.L, N, p.periodic, p.t, dim, cnt, A->kbits[sp]);
+    FD_LAUNCHED(ctx);
+    FD_TRY(exclusive_scan(ctx, cnt, dim, A->kptr[sp]));
+    int64_t nh = 0;
+    FD_CUDA(ctx, cudaMemcpyAsync(&nh, A->kptr[sp] + dim, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    FD_CUDA(ctx, cudaStreamSynchronize(st));
+    cudaFree(cnt);
+    const size_t m = (size_t)std::max<int64_t>(nh, 1);
+    FD_CUDA(ctx, cudaMalloc(&A->kcol[sp], sizeof(int32_t) * m));
+    FD_CUDA(ctx, cudaMalloc(&A->kval[sp], sizeof(double) * m));
+    FD_CUDA(ctx, cudaMalloc(&A->kval32[sp], sizeof(float) * m));
+    k_kron_fill<<<(unsigned)cdiv(dim, T), T, 0, st>>>(p.L, N, p.periodic, p.t, dim, A->kptr[sp], A->kcol[sp],
+                                                      A->kval[sp], A->kval32[sp]);
+    FD_LAUNCHED(ctx);
+  }
+  double dg[25];
+  float dg32[25];
+  for (int n = 0; n <= 24; ++n) {
+    dg[n] = p.U * (double)n;  // the generator's U * popcount
+    dg32[n] = (float)dg[n];   // as the FP32 copy of the stored values
+  }
+  FD_CUDA(ctx, cudaMalloc(&A->kdiag, sizeof(dg)));
+  FD_CUDA(ctx, cudaMalloc(&A->kdiag32, sizeof(dg32)));
+  FD_CUDA(ctx, cudaMemcpyAsync(A->kdiag, dg, sizeof(dg), cudaMemcpyHostToDevice, st));
+  FD_CUDA(ctx, cudaMemcpyAsync(A->kdiag32, dg32, sizeof(dg32), cudaMemcpyHostToDevice, st));
+  FD_CUDA(ctx, cudaStreamSynchronize(st));
+  A->kron = 1;
+  return FD_OK;
+}
+
 fd_status fd_build_matrix(fd_ctx* ctx, const char* spec, fd_matrix** out) {
   return fd_build_matrix_sell(ctx, spec, 32, 1, out);
 }
@@ -753,6 +841,8 @@ fd_status fd_build_matrix_sell(fd_ctx* ctx, const char* spec, int C, int sigma,
   int32_t* col = nullptr;
   double* val = nullptr;
   int64_t nnz = 0;
+  bool kron_flag = false;
+  HubbardP hub{};
 
   if (s.kind == "hubbard") {
     long long L, nu, nd;
@@ -769,6 +859,12 @@ fd_status fd_build_matrix_sell(fd_ctx* ctx, const char* spec, int C, int sigma,
       delete A;
       return set_err(ctx, FD_ERR_ARG, "hubbard: need 2 <= n_sites <= 24 (>= 3 periodic), 0 <= n <= n_sites, bc open|periodic");
     }
+    long long kron;
+    if (!get_int(s, "kron", &kron, false, 0) || kron < 0 || kron > 1 || (kron && sigma != 1)) {
+      delete A;
+      return set_err(ctx, FD_ERR_ARG, "hubbard: kron must be 0 or 1, and kron=1 needs sigma = 1");
+    }
+    kron_flag = kron == 1;
     HubbardP p;
     p.L = (int)L; p.Nu = (int)nu; p.Nd = (int)nd; p.periodic = bcs == "periodic";
     p.dim_up = binom(p.L, p.Nu); p.dim_dn = binom(p.L, p.Nd);
@@ -788,6 +884,7 @@ fd_status fd_build_matrix_sell(fd_ctx* ctx, const char* spec, int C, int sigma,
     FD_CUDA(ctx, cudaMalloc(&val, sizeof(double) * nnz));
     k_hubbard_fill<<<(unsigned)cdiv(p.D, T), T, 0, st>>>(p, rowptr, col, val);
     FD_LAUNCHED(ctx);
+    hub = p;
   } else if (s.kind == "anderson3d") {
     long long L, seed;
     double W, t;
@@ -850,7 +947,16 @@ fd_status fd_build_matrix_sell(fd_ctx* ctx, const char* spec, int C, int sigma,
     delete A;
     return set_err(ctx, FD_ERR_ARG, "unknown matrix kind '%s'", s.kind.c_str());
   }
-  return finish_build(ctx, A, rowptr, col, val, nnz, out);
+  FD_TRY(finish_build(ctx, A, rowptr, col, val, nnz, out));
+  if (kron_flag) {
+    const fd_status st = build_kron(ctx, *out, hub);
+    if (st != FD_OK) {
+      fd_matrix_free(*out);
+      *out = nullptr;
+      return st;
+    }
+  }
+  return FD_OK;
 }
 
 fd_status fd_matrix_from_csr(fd_ctx* ctx, int64_t D, const int64_t* rowptr, const int32_t* col,
@@ -898,6 +1004,11 @@ fd_status fd_matrix_free(fd_matrix* A) {
   cudaDeviceSynchronize();
   cudaFree(A->chunk_ptr); cudaFree(A->row_len); cudaFree(A->col); cudaFree(A->val);
   cudaFree(A->val32); cudaFree(A->perm); cudaFree(A->iperm); cudaFree(A->diag_added);
+  for (int sp = 0; sp < 2; ++sp) {
+    cudaFree(A->kbits[sp]); cudaFree(A->kptr[sp]); cudaFree(A->kcol[sp]);
+    cudaFree(A->kval[sp]); cudaFree(A->kval32[sp]);
+  }
+  cudaFree(A->kdiag); cudaFree(A->kdiag32);
   delete A;
   return FD_OK;
 }

@@ -258,6 +258,110 @@ __device__ __forceinline__ void cheb_rows(const SellArgs<T>& A, const StepArgs<T
   }
 }
 
+// ---------------------------------------------------------------------------
+// Matrix-free Hubbard operator (Sec. 4 runs FD on Hubbard matrices; the
+// paper's production runs apply them without storing them):
+//   (H x)_(u,d) = U n(u,d) x_(u,d) + sum_u' h_up(u,u') x_(u',d)
+//                                  + sum_d' h_dn(d,d') x_(u,d')
+// with row (u, d) = u * dim_dn + d.  The up-spin hops of consecutive rows
+// (u, d), (u, d + 1) read consecutive rows (u', d), (u', d + 1): whole
+// coalesced row blocks; the down-spin hops stay inside the u slab.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct KronArgs {
+  int64_t D, dim_dn;
+  const uint32_t* bits_up;
+  const uint32_t* bits_dn;
+  const int64_t* ptr_up;
+  const int32_t* col_up;
+  const T* val_up;
+  const int64_t* ptr_dn;
+  const int32_t* col_dn;
+  const T* val_dn;
+  const T* diag;  // 25 entries: U * n for n doubly occupied sites
+};
+
+// s = sum_j h_ij x_j for row (u, d), the entries in the order of the stored
+// row (diagonal first, then ascending columns: the up hops to u' < u, the
+// down hops, the up hops to u' > u), so the sums round as in the SELL kernel
+template <typename T, int NB>
+__device__ __forceinline__ void kron_row_product(const KronArgs<T>& K, const T* __restrict__ X, int64_t ldx,
+                                                 int64_t row, int gl, V16<T> (&acc)[Layout<T, NB>::CPL],
+                                                 V16<T> (&xi)[Layout<T, NB>::CPL]) {
+  using L = Layout<T, NB>;
+  constexpr int E = L::E;
+  const T* xl = X + gl * E;
+  const int64_t u = row / K.dim_dn, d = row - u * K.dim_dn;
+  const T dg = K.diag[__popc(K.bits_up[u] & K.bits_dn[d])];
+#pragma unroll
+  for (int v = 0; v < L::CPL; ++v) {
+    xi[v].ldg(xl + row * ldx + v * L::G * E);
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[v].v[e] = dg * xi[v].v[e];
+  }
+  auto add = [&](T a, int64_t r) {
+#pragma unroll
+    for (int v = 0; v < L::CPL; ++v) {
+      V16<T> x;
+      x.ldg(xl + r * ldx + v * L::G * E);
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[v].v[e] = fma(a, x.v[e], acc[v].v[e]);
+    }
+  };
+  int64_t k = K.ptr_up[u];
+  const int64_t ke = K.ptr_up[u + 1];
+  for (; k < ke && K.col_up[k] < u; ++k) add(K.val_up[k], (int64_t)K.col_up[k] * K.dim_dn + d);
+  const int64_t kd1 = K.ptr_dn[d + 1];
+  for (int64_t kd = K.ptr_dn[d]; kd < kd1; ++kd) add(K.val_dn[kd], u * K.dim_dn + K.col_dn[kd]);
+  for (; k < ke; ++k) add(K.val_up[k], (int64_t)K.col_up[k] * K.dim_dn + d);
+}
+
+// One fused Chebyshev step with the matrix-free Hubbard operator; the same
+// operand loads and epilogue as cheb_rows
+template <typename T, int NB, int MODE>
+__device__ __forceinline__ void kron_rows(const KronArgs<T>& K, const StepArgs<T>& s, int64_t row0) {
+  using L = Layout<T, NB>;
+  constexpr int E = L::E;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / L::G, gl = lane % L::G;
+  const int64_t row = row0 + g;
+  if (row >= K.D) return;  // no warp-wide operations follow
+  V16<T> z[L::CPL], vin[L::CPL];
+  if (MODE != MODE_SPMMV) {
+#pragma unroll
+    for (int v = 0; v < L::CPL; ++v) {
+      const int64_t off = gl * E + v * L::G * E;
+      z[v].ldcs(s.Z + row * s.ldz + off);
+      if (MODE == MODE_GENERIC) vin[v].ldcs(s.Vin + row * s.ldvi + off);
+    }
+  }
+  V16<T> acc[L::CPL], xi[L::CPL];
+  kron_row_product<T, NB>(K, s.X, s.ldx, row, gl, acc, xi);
+#pragma unroll
+  for (int v = 0; v < L::CPL; ++v) {
+    const int64_t off = gl * E + v * L::G * E;
+    V16<T> y;
+    if (MODE == MODE_SPMMV) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) y.v[e] = s.c_ax * acc[v].v[e] + s.c_x * xi[v].v[e];
+      y.st(s.Y + row * s.ldy + off);
+    } else {
+      V16<T> o;
+#pragma unroll
+      for (int e = 0; e < E; ++e) y.v[e] = s.c_ax * acc[v].v[e] + s.c_x * xi[v].v[e] - z[v].v[e];
+      if (MODE == MODE_SECOND) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          o.v[e] = s.mu0 * z[v].v[e] + s.mu1 * xi[v].v[e] + s.mu2 * y.v[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) o.v[e] = vin[v].v[e] + s.mu2 * y.v[e];
+      }
+      if (s.Y) y.st(s.Y + row * s.ldy + off);
+      o.stcs(s.Vout + row * s.ldvo + off);
+    }
+  }
+}
 
 }  // namespace step
 }  // namespace fdi

@@ -1,0 +1,110 @@
+"""Matrix-free Hubbard operator (spec flag kron=1) against the oracle and against
+the stored-matrix (SELL) kernel on the same matrix."""
+import numpy as np
+import pytest
+
+import fd_inputs
+from gpu_util import U32, U64, filter_tolerance
+from oracle import chebyshev as ch
+from oracle import lanczos
+from oracle import matrices as mat
+
+pytestmark = pytest.mark.gpu
+
+SPECS = ["hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open",
+         "hubbard:n_sites=7,n_up=3,n_dn=2,t=1,U=4.3,bc=periodic",
+         "hubbard:n_sites=10,n_up=5,n_dn=0,t=1,U=4,bc=open",     # one down state
+         "hubbard:n_sites=6,n_up=0,n_dn=3,t=0.7,U=2,bc=periodic"]  # one up state
+
+
+@pytest.fixture(scope="module")
+def fd():
+    import paper_2209_01974_gb300 as fd
+    return fd
+
+
+@pytest.fixture(scope="module")
+def ctx(fd):
+    return fd.fd_create(0)
+
+
+def _filter(fd, ctx, A, V0, mu, alpha, beta, dtype):
+    import torch
+    V = torch.from_numpy(V0).to(dtype).cuda()
+    W1, W2 = torch.empty_like(V), torch.empty_like(V)
+    fd.fd_filter(ctx, A, V, mu, alpha, beta, W1, W2)
+    return V.cpu().numpy().astype(np.float64)
+
+
+def _params(csr, n, seed):
+    lo, hi = lanczos.gershgorin(csr)
+    alpha, beta = ch.scale_params(lo - 0.01, hi + 0.01)
+    w = np.random.default_rng(seed).uniform(-0.6, 0.4)
+    return ch.filter_coeffs(w, w + 0.3, n), alpha, beta
+
+
+@pytest.mark.parametrize("spec", SPECS)
+@pytest.mark.parametrize("nb", [4, 16, 64])
+@pytest.mark.parametrize("n", [2, 3, 25])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_kron_filter_matches_oracle(fd, ctx, spec, nb, n, prec):
+    import torch
+    csr = mat.build(spec)
+    A = fd.fd_build_matrix(ctx, spec + ",kron=1")
+    D = len(csr[0]) - 1
+    V0 = fd_inputs.random_block(D, nb, 5 * nb + n)
+    if prec == "f32":
+        V0 = V0.astype(np.float32).astype(np.float64)
+    mu, alpha, beta = _params(csr, n, nb)
+    got = _filter(fd, ctx, A, V0, mu, alpha, beta, torch.float64 if prec == "f64" else torch.float32)
+    ref = ch.cheb_filter(mat.to_scipy(csr), V0, mu, alpha, beta)
+    tol = filter_tolerance(csr, mu, alpha, beta, V0, U64 if prec == "f64" else U32)
+    assert np.all(np.abs(got - ref) <= tol)
+
+
+@pytest.mark.parametrize("spec", SPECS)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_kron_filter_equals_stored_matrix_kernel(fd, ctx, spec, prec):
+    # same entries summed in the same order as the SELL row: identical results
+    import torch
+    csr = mat.build(spec)
+    D = len(csr[0]) - 1
+    V0 = fd_inputs.random_block(D, 32, 9)
+    mu, alpha, beta = _params(csr, 20, 2)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    a = _filter(fd, ctx, fd.fd_build_matrix(ctx, spec + ",kron=1"), V0, mu, alpha, beta, dt)
+    b = _filter(fd, ctx, fd.fd_build_matrix(ctx, spec), V0, mu, alpha, beta, dt)
+    assert np.array_equal(a, b)
+
+
+def test_kron_spmmv_matches_oracle(fd, ctx):
+    import torch
+    spec = SPECS[1]
+    csr = mat.build(spec)
+    A = fd.fd_build_matrix(ctx, spec + ",kron=1")
+    D = len(csr[0]) - 1
+    X0 = fd_inputs.random_block(D, 64, 3)
+    X = torch.from_numpy(X0).cuda()
+    Y = torch.empty_like(X)
+    fd.fd_spmmv(ctx, A, X, Y)
+    S = mat.to_scipy(csr)
+    nnz_row = np.diff(csr[0]).max()
+    assert np.all(np.abs(Y.cpu().numpy() - S @ X0) <= nnz_row * U64 * (abs(S) @ np.abs(X0)) + 1e-300)
+
+
+def test_kron_solve_matches_dense(fd, ctx):
+    spec = "hubbard:n_sites=6,n_up=3,n_dn=3,t=1,U=4,bc=open"
+    A = fd.fd_build_matrix(ctx, spec + ",kron=1")
+    lam = np.linalg.eigvalsh(mat.to_scipy(mat.build(spec)).toarray())
+    th, rho, res = fd.fd_solve(ctx, A, 2.0, 3.0, 8, 8, 60, 1e-9)
+    tau = 2.5
+    want = np.sort(lam[np.argsort(np.abs(lam - tau), kind="stable")[:8]])
+    assert np.all(rho <= 1e-9)
+    assert np.max(np.abs(np.sort(th) - want)) <= 1e-10 * np.abs(lam).max()
+
+
+def test_kron_needs_original_order(fd, ctx):
+    with pytest.raises(fd.FDError):
+        fd.fd_build_matrix(ctx, SPECS[0] + ",kron=1", C=32, sigma=64)
+    with pytest.raises(fd.FDError):
+        fd.fd_build_matrix(ctx, SPECS[0] + ",kron=2")
