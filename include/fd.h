@@ -77,7 +77,12 @@ int64_t fd_kernel_launches(const fd_ctx* ctx);
 
 /* Build a test matrix on the device from a parameter string (the paper names
  * its matrices by ScaMaC parameter strings, Sec. 3.2; Table 2):
- *   "hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open"     (bc = open|periodic)
+ *   "hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open"     (bc = open|periodic;
+ *                                       kron=1 also builds the per-spin hopping
+ *                                       tables: fd_filter and fd_spmmv then apply
+ *                                       H = H_up x 1 + 1 x H_dn + U n_double without
+ *                                       the stored matrix, with results equal to
+ *                                       the stored-matrix kernel; needs sigma = 1)
  *   "anderson3d:L=128,W=2,seed=1,t=1"   periodic cubic lattice, eps_i = W (u_i - 1/2)
  *   "chain:n=1000,t=1"                  open tight-binding chain
  *   "roadgraph:side=2000,q=0.3,seed=0"  Laplacian of a road-like planar graph on a
