@@ -339,6 +339,8 @@ KERNEL_WORKLOADS = {
     "stencil": SPEC,
     "hubbard14": "hubbard:n_sites=14,n_up=7,n_dn=7,t=1,U=4,bc=periodic",
     "hubbard14kron": "hubbard:n_sites=14,n_up=7,n_dn=7,t=1,U=4,bc=periodic,kron=1",
+    "hubbard12": "hubbard:n_sites=12,n_up=6,n_dn=6,t=1,U=4,bc=periodic",
+    "hubbard12kron": "hubbard:n_sites=12,n_up=6,n_dn=6,t=1,U=4,bc=periodic,kron=1",
     "roadgraph": "roadgraph:side=2000,q=0.3,seed=0",
 }
 
