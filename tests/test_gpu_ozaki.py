@@ -127,3 +127,31 @@ def test_bounded_wait_gives_up_and_context_stays_usable(fd, ctx):
     fd.fd_set_gemm_mode(ctx, "ozaki")
     C = fd.fd_gram(ctx, _t(X), _t(X)).cpu().numpy()
     assert np.all(np.abs(C - X.T @ X) <= _bound(X, X))
+
+
+def test_full_size_gram_and_cholqr2(fd, ctx):
+    # the bench's block, 2,097,152 x 384: sampled Gram entries against CPU dot
+    # products, then the orthonormality of CholQR2 (tensor-core products) checked
+    # with the FP64-arithmetic Gram
+    import torch
+    D, ns = 2097152, 384
+    g = torch.Generator(device="cuda").manual_seed(7)
+    V = torch.randn((D, ns), dtype=torch.float64, device="cuda", generator=g)
+    V[:, 100] *= 1e3  # columns of very different scale
+    fd.fd_set_gemm_mode(ctx, "auto")
+    G = fd.fd_gram(ctx, V, V).cpu().numpy()
+    pairs = [(0, 0), (0, 383), (100, 100), (100, 7), (250, 251), (383, 17)]
+    cols = {c: V[:, c].cpu().numpy() for c in {c for p in pairs for c in p}}
+    for i, j in pairs:
+        x, y = cols[i], cols[j]
+        ref = float(np.dot(x, y))
+        # split error + the CPU sum's own rounding: under 8 K u max|x| max|y|
+        assert abs(G[i, j] - ref) <= 8 * D * U * np.abs(x).max() * np.abs(y).max()
+    fd.fd_orthonormalize(ctx, V)
+    fd.fd_set_gemm_mode(ctx, "fp64")
+    Q = fd.fd_gram(ctx, V, V).cpu().numpy()
+    fd.fd_set_gemm_mode(ctx, "auto")
+    # the FP64 check Gram rounds each entry by about sqrt(D) u (blocked sums)
+    assert np.abs(Q - np.eye(ns)).max() <= 1e-12
+    del V
+    torch.cuda.empty_cache()
