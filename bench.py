@@ -52,7 +52,7 @@ FP64_TFLOPS = 1.25
 # DRAM bytes (read + write) of one generic FP32 step of this workload, from one ncu
 # capture of `bench.py --kernel-only f32` (profiles/k_cheb_step_f32_stencil_L128_nb64.md);
 # set to None whenever the step kernel changes
-TRAFFIC_F32 = 1.762288e9 + 1.027285e9
+TRAFFIC_F32 = 1.762259e9 + 1.027703e9
 
 
 def filter_bytes(D, nnz, nb, n, Sx):

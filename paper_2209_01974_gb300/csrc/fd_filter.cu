@@ -26,9 +26,10 @@ namespace {
 using namespace step;
 
 template <typename T, int NB, int MODE>
-__global__ void __launch_bounds__(WARPS * 32, sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64)
+__global__ void __launch_bounds__(step_warps<T>() * 32, sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64)
     k_cheb_step(SellArgs<T> A, StepArgs<T> s, unsigned pf) {
   using L = Layout<T, NB>;
+  constexpr int WARPS = step_warps<T>();
   // L2 prefetch for the CTA that starts one resident wave (pf CTAs) later:
   // its first loads (row-wise operands, then the SELL slab they index) are a
   // chain of dependent DRAM round trips that no register budget can overlap.
@@ -102,13 +103,14 @@ fd_status launch_step(fd_ctx* ctx, const fd_matrix* M, int mode, const StepArgs<
   SellArgs<T> A;
   A.chunk_ptr = M->chunk_ptr; A.row_len = M->row_len; A.col = M->col; A.D = M->D; A.C = M->C;
   if constexpr (sizeof(T) == 8) A.val = (const T*)M->val; else A.val = (const T*)M->val32;
-  const int64_t rows_per_block = (int64_t)WARPS * L::RPW;
+  constexpr int SW = step_warps<T>();
+  const int64_t rows_per_block = (int64_t)SW * L::RPW;
   const unsigned grid = (unsigned)cdiv(M->D, rows_per_block);
   // prefetch distance: one wave of resident CTAs (the launch-bounds occupancy)
   const unsigned pf = (unsigned)ctx->num_sms * (sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64);
-  if (mode == MODE_SPMMV) k_cheb_step<T, NB, MODE_SPMMV><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s, pf);
-  else if (mode == MODE_SECOND) k_cheb_step<T, NB, MODE_SECOND><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s, pf);
-  else k_cheb_step<T, NB, MODE_GENERIC><<<grid, WARPS * 32, 0, ctx->stream>>>(A, s, pf);
+  if (mode == MODE_SPMMV) k_cheb_step<T, NB, MODE_SPMMV><<<grid, SW * 32, 0, ctx->stream>>>(A, s, pf);
+  else if (mode == MODE_SECOND) k_cheb_step<T, NB, MODE_SECOND><<<grid, SW * 32, 0, ctx->stream>>>(A, s, pf);
+  else k_cheb_step<T, NB, MODE_GENERIC><<<grid, SW * 32, 0, ctx->stream>>>(A, s, pf);
   FD_LAUNCHED(ctx);
   return FD_OK;
 }

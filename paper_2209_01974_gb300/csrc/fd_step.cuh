@@ -83,8 +83,12 @@ struct StepArgs {
 
 constexpr int WARPS = 8;
 constexpr int BATCH = 4;   // entries per batch; SELL chunk lengths are multiples of 8
-constexpr int MIN_BLOCKS = 6;  // FP32 steps: >= 48 resident warps per SM (<= 40 registers)
-constexpr int MIN_BLOCKS_F64 = 4;  // FP64 steps keep 64 registers (FP64-ALU bound anyway)
+constexpr int MIN_BLOCKS = 12;     // FP32 steps: 4-warp CTAs, 48 resident warps per SM (<= 40 registers)
+constexpr int MIN_BLOCKS_F64 = 4;  // FP64 steps: 8-warp CTAs with 64 registers (FP64-ALU bound anyway)
+// warps per CTA of the fused step (k_cheb_step): smaller CTAs for FP32 (more of
+// them in flight, a finer L2 prefetch granule), 8 for FP64
+template <typename T>
+__host__ __device__ constexpr int step_warps() { return sizeof(T) == 4 ? 4 : WARPS; }
 
 template <typename T, int NB>
 struct Layout {
