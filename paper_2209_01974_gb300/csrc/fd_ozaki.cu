@@ -38,6 +38,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "fd_internal.cuh"
@@ -629,13 +630,16 @@ __global__ void k_wait_unsatisfied(long long limit, int* err) {
   if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(err, 1);
 }
 
-bool attrs_set = false;
+// bit d: the shared-memory attribute is set on device d (a function attribute
+// is per device; setting it twice is harmless, so racing threads only repeat it)
+std::atomic<unsigned long long> attrs_set{0};
 
 fd_status set_attrs(fd_ctx* ctx) {
-  if (attrs_set) return FD_OK;
+  const unsigned long long bit = ctx->device < 64 ? 1ull << ctx->device : 0ull;
+  if (bit && (attrs_set.load() & bit)) return FD_OK;
   FD_CUDA(ctx, cudaFuncSetAttribute(k_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM));
   FD_CUDA(ctx, cudaFuncSetAttribute(k_oz_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM));
-  attrs_set = true;
+  attrs_set.fetch_or(bit);
   return FD_OK;
 }
 
