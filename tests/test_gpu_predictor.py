@@ -128,7 +128,7 @@ def test_trained_predictor_beats_heuristic_on_heldout_problems(fd, ctx):
                                   max_outer=40, n_max=3000)
         r1 = predictor.solve_with(ctx, params, A, a, b, nt, log["nb"], log["degree"], log["tol"], sd,
                                   max_outer=40, n_max=3000)
-        assert r1[2]["converged"] == 1 and r1[1].max() <= log["tol"]   # converged residuals judge it
+        assert r1[2]["converged"] == 1 and r1[1].max() <= log["tol"]   # converged residuals decide
         h_tot += r0[2]["n_spmmv"]
         l_tot += r1[2]["n_spmmv"]
     print(f"held-out SpMMVs: heuristic {h_tot}, learned {l_tot} ({100 * (1 - l_tot / h_tot):.1f}% fewer)")
