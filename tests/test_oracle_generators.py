@@ -179,3 +179,21 @@ def test_instance_sizes_agree_with_input_generator():
     import fd_inputs
     for s in range(64):
         assert fd_inputs.anderson_instance(s) == mat.anderson_instance(s)
+
+
+@pytest.mark.parametrize("L,nu,nd,bc", [(6, 3, 3, "open"), (7, 3, 2, "periodic"), (8, 4, 1, "periodic"),
+                                        (5, 0, 2, "open"), (6, 2, 0, "periodic")])
+def test_hubbard_is_a_kronecker_sum(L, nu, nd, bc):
+    # with all up operators ordered before all down ones, a hop of either spin
+    # passes only fermions of its own spin, so the matrix factorises as
+    # H = H_up x 1 + 1 x H_dn + U n_double in the row order rank_up * dim_dn + rank_dn
+    import scipy.sparse as sp
+    t, U = 1.3, 4.2
+    h_up = mat.to_scipy(mat.hubbard(L, nu, 0, t, 0.0, bc))
+    h_dn = mat.to_scipy(mat.hubbard(L, nd, 0, t, 0.0, bc))
+    bu, bd = mat.spin_basis(L, nu), mat.spin_basis(L, nd)
+    n_double = np.array([bin(int(a) & int(b)).count("1") for a in bu for b in bd], dtype=np.float64)
+    K = sp.kron(h_up, sp.identity(len(bd))) + sp.kron(sp.identity(len(bu)), h_dn) + sp.diags(U * n_double)
+    H = mat.to_scipy(mat.hubbard(L, nu, nd, t, U, bc))
+    assert H.shape == K.shape
+    assert abs(H - K).max() == 0.0
