@@ -53,3 +53,12 @@ def metrics(csr, n_p):
     chi2 = float(n_vc.sum()) / D
     chi3 = n_p * float(n_vc.max()) / D
     return chi1, chi2, chi3, n_vc, n_vm
+
+
+def volumes(n_vc, n_p, n_b, S_d):
+    """Average and maximal communication volume per process and SpMV in bytes
+    (Sec. 3.1, Eqs. VCAve and VCMax): V = n_b S_d n_vc per process, so
+    V_ave = n_b S_d sum_p n_vc / N_p = n_b D S_d chi_2 / N_p and
+    V_max = n_b S_d max_p n_vc = n_b D S_d chi_3 / N_p."""
+    n_vc = np.asarray(n_vc, dtype=np.int64)
+    return n_b * S_d * float(n_vc.sum()) / n_p, float(n_b * S_d * int(n_vc.max()))

@@ -73,3 +73,26 @@ def test_paper_tables(fd, ctx, spec, gold):
         assert abs(c1 - chi13) <= 0.005 + 1e-12, (n_p, c1, chi13)
         assert abs(c3 - chi13) <= 0.005 + 1e-12, (n_p, c3, chi13)
         assert abs(c2 - chi2) <= 0.005 + 1e-12, (n_p, c2, chi2)
+
+
+def table3_rows():
+    rows = []
+    for line in open(os.path.join(GOLD, "table3_commvol_hubbard14.txt")):
+        if line.strip() and not line.startswith("#"):
+            n_p, avg, mx, unit = line.split()
+            rows.append((int(n_p), float(avg), float(mx), 2.0 ** 30 if unit == "GiB" else 2.0 ** 20))
+    return rows
+
+
+def check_table3(counts):
+    # counts(n_p) -> n_vc per process; volumes of 64 FP64 vectors against the
+    # printed values, to half a unit of their last printed digit
+    for n_p, avg, mx, scale in table3_rows():
+        a, m = comm.volumes(counts(n_p), n_p, 64, 8)
+        assert abs(a / scale - avg) <= 0.005 + 1e-9, (n_p, a / scale, avg)
+        assert abs(m / scale - mx) <= 0.005 + 1e-9, (n_p, m / scale, mx)
+
+
+def test_paper_table3_volumes(fd, ctx):
+    A = fd.fd_build_matrix(ctx, "hubbard:n_sites=14,n_up=7,n_dn=7,t=1,U=4,bc=open", C=64, sigma=1)
+    check_table3(lambda n_p: fd.fd_comm_metrics(ctx, A, n_p)[3])

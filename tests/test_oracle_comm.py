@@ -76,3 +76,15 @@ def test_spin_chain_matches_table7():
         assert abs(c3 - chi13) <= 0.005 + 1e-12, (n_p, c3, chi13)
         assert abs(c1 - chi13) <= 0.005 + 1e-12, (n_p, c1, chi13)
         assert abs(c2 - chi2) <= 0.005 + 1e-12, (n_p, c2, chi2)
+
+
+def test_volumes_closed_form():
+    # open chain: interior processes read 2 remote entries, the ends 1
+    csr = mat.chain(1000)
+    n_vc, _ = comm.counts(csr, 4)
+    avg, mx = comm.volumes(n_vc, 4, 64, 8)
+    assert avg == 64 * 8 * (1 + 2 + 2 + 1) / 4
+    assert mx == 64 * 8 * 2
+    chi1, chi2, chi3, _, _ = comm.metrics(csr, 4)
+    assert avg == pytest.approx(64 * 1000 * 8 * chi2 / 4)
+    assert mx == pytest.approx(64 * 1000 * 8 * chi3 / 4)
