@@ -66,7 +66,7 @@ def test_counts_match_brute_force(D, n_p, seed):
         assert comm.metrics(csr, 1)[:3] == (0.0, 0.0, 0.0)
 
 
-def test_spin_chain_matches_table7():
+def test_spin_chain_matches_tables_7_and_9():
     # the 24-site chain with 12 particles: the hopping pattern of SpinChainXXZ
     csr = mat.build("hubbard:n_sites=24,n_up=12,n_dn=0,t=1,U=4,bc=open")
     assert len(csr[0]) - 1 == 2704156
@@ -76,6 +76,13 @@ def test_spin_chain_matches_table7():
         assert abs(c3 - chi13) <= 0.005 + 1e-12, (n_p, c3, chi13)
         assert abs(c1 - chi13) <= 0.005 + 1e-12, (n_p, c1, chi13)
         assert abs(c2 - chi2) <= 0.005 + 1e-12, (n_p, c2, chi2)
+    # Table 9: the same counts as volumes of 64 FP64 vectors, to half a unit of
+    # the last printed digit (0.1 MiB)
+    for n_p, avg, mx in np.loadtxt(os.path.join(GOLD, "table9_commvol_spinchain24.txt")):
+        n_vc, _ = comm.counts(csr, int(n_p))
+        a, m = comm.volumes(n_vc, int(n_p), 64, 8)
+        assert abs(a / 2 ** 20 - avg) <= 0.05 + 1e-9, (n_p, a / 2 ** 20, avg)
+        assert abs(m / 2 ** 20 - mx) <= 0.05 + 1e-9, (n_p, m / 2 ** 20, mx)
 
 
 def test_volumes_closed_form():
