@@ -72,6 +72,19 @@ fd_status fd_set_stream(fd_ctx* ctx, void* stream);
 const char* fd_last_error(const fd_ctx* ctx);
 /* Number of kernels this context has launched since creation (for audits). */
 int64_t fd_kernel_launches(const fd_ctx* ctx);
+/* Device memory held by the context's grow-only workspaces (HOST outputs,
+ * either may be NULL): the bytes held now and the number of cudaMalloc calls
+ * made for them since creation.  The paper has no counterpart; callers use it
+ * to audit the library's allocations. */
+fd_status fd_workspace_info(const fd_ctx* ctx, size_t* bytes_held, int64_t* allocations);
+/* Cap the bytes the context's workspaces may hold together (0 = no cap, the
+ * default).  A workspace that would grow beyond the cap is refused before
+ * anything is freed or allocated and the call needing it returns FD_ERR_OOM,
+ * exactly as when cudaMalloc fails; the tensor-core products instead fall
+ * back to FP64 arithmetic when their digit workspace is refused.  Lets a
+ * caller bound the library's memory (and tests inject an allocation failure
+ * from the host). */
+fd_status fd_set_workspace_limit(fd_ctx* ctx, size_t limit_bytes);
 
 /* ------------------------------------------------------------------ matrices */
 
@@ -248,7 +261,11 @@ fd_status fd_orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns,
  * device, with that device current); make that first call before any stream
  * capture.  Every call shares the one array: calls that overlap on the GPU
  * (other host threads, other streams) race and must be serialised by the
- * caller.  It never calls cudaMalloc or cudaFree. */
+ * caller.  Every product runs in FP64 arithmetic (the tensor-core products
+ * need digit workspaces), whatever fd_set_gemm_mode selected, and the call
+ * synchronises the context's stream once per pass (the pivot check).  It
+ * never calls cudaMalloc or cudaFree and leaves the context's workspaces
+ * untouched (fd_workspace_info reports the same before and after). */
 fd_status fd_orthonormalize_noalloc(fd_ctx* ctx, double* V, int64_t D, int ns,
                                     int64_t ldv, double* R, int* passes);
 

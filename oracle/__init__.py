@@ -26,5 +26,7 @@ ortho        Cholesky-QR 2 with shifted fallback (Sec. 2 orthogonalisation)
 rayleigh_ritz  Ritz pairs and residual norms (Sec. 2)
 fd           the FD outer loop (Sec. 2, Alg. 1) with the interval/degree heuristic
 kpm          kernel-polynomial density-of-states moments (Sec. 4.1)
-sell         SELL-C-sigma layout rules used to check the device matrix
+lehmann      Lehmann bounds of the eigenvalues nearest a shift (Sec. 2 intervals)
+comm         communication metrics chi_1..3 and volumes of distributed SpMV (Sec. 3.1)
+mlp          the filter-parameter perceptron: forward, gradient, Adam
 """

@@ -63,6 +63,8 @@ _SIGS = {
     "fd_set_stream": (_i32, [_vp, _vp]),
     "fd_last_error": (ctypes.c_char_p, [_vp]),
     "fd_kernel_launches": (_i64, [_vp]),
+    "fd_workspace_info": (_i32, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i64)]),
+    "fd_set_workspace_limit": (_i32, [_vp, ctypes.c_size_t]),
     "fd_build_matrix": (_i32, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)]),
     "fd_build_matrix_sell": (_i32, [_vp, ctypes.c_char_p, _i32, _i32, ctypes.POINTER(_vp)]),
     "fd_matrix_from_csr": (_i32, [_vp, _i64, _pi64, _pi32, _pd, _i32, _i32, ctypes.POINTER(_vp)]),
@@ -170,6 +172,13 @@ class Ctx:
     def kernel_launches(self):
         return _lib.fd_kernel_launches(self.handle)
 
+    @property
+    def workspace(self):
+        """(bytes held by the grow-only workspaces, cudaMalloc calls made for them)."""
+        b, n = ctypes.c_size_t(0), _i64(0)
+        _check(self, _lib.fd_workspace_info(self.handle, ctypes.byref(b), ctypes.byref(n)))
+        return b.value, n.value
+
 
 class Matrix:
     def __init__(self, ctx, handle):
@@ -275,6 +284,11 @@ def fd_spmmv(ctx, A, X, Y):
 
 
 FD_GEMM_AUTO, FD_GEMM_FP64, FD_GEMM_OZAKI = 0, 1, 2
+
+
+def fd_set_workspace_limit(ctx, limit_bytes):
+    """Cap the context's workspace bytes (0 = no cap); growth beyond it is FD_ERR_OOM."""
+    _check(ctx, _lib.fd_set_workspace_limit(ctx.handle, int(limit_bytes)))
 
 
 def fd_set_gemm_mode(ctx, mode):

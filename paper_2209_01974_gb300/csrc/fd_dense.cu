@@ -505,6 +505,11 @@ fd_status rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const do
     FD_TRY(oz_rotate(ctx, V, ldv, D, n, M, upper, &used));
     if (used) return FD_OK;
   }
+  return rotate_fp64(ctx, V, ldv, D, n, M, upper);
+}
+
+fd_status rotate_fp64(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M,
+                      bool upper) {
   const size_t smem = sizeof(double) * RT * n;
   if (smem > ctx->smem_optin) return set_err(ctx, FD_ERR_ARG, "block too wide for rotation (%d)", n);
   if (smem > 48 * 1024)

@@ -22,6 +22,9 @@ struct fd_ctx {
   int gemm_mode = 0;  // fd_gemm_mode: 0 auto, 1 FP64 arithmetic, 2 bf16 tensor-core splitting
   // grow-only device workspaces keyed by purpose
   std::unordered_map<std::string, std::pair<void*, size_t>> ws;
+  size_t ws_bytes = 0;      // bytes the workspaces hold now
+  int64_t ws_allocs = 0;    // cudaMalloc calls made for workspaces
+  size_t ws_limit = 0;      // cap on ws_bytes (0 = none): growth beyond it fails with FD_ERR_OOM
   // pinned host staging
   void* host_stage = nullptr;
   size_t host_stage_bytes = 0;
@@ -128,6 +131,10 @@ fd_status small_gemm_dev(fd_ctx* ctx, const double* A, const double* B, double* 
 // V (D x n, ldv) <- V * M, M n x n row-major; upper = M upper triangular
 fd_status rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M,
                  bool upper);
+// the same rotation with FP64 arithmetic only (in place, shared-memory rows;
+// allocates nothing, whatever the gemm mode)
+fd_status rotate_fp64(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const double* M,
+                      bool upper);
 // Cholesky of the n x n SPD matrix G (device), upper factor into R; status into
 // *ok_dev (1 ok / 0 failed); shift added to the diagonal before factorising.
 fd_status cholesky(fd_ctx* ctx, const double* G, int n, double shift_rel_trace_coeff,

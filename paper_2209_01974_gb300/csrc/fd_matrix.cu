@@ -30,16 +30,23 @@ fd_status set_err(fd_ctx* ctx, fd_status st, const char* fmt, ...) {
 fd_status workspace(fd_ctx* ctx, const char* name, size_t bytes, void** out) {
   auto& e = ctx->ws[name];
   if (e.second < bytes) {
+    size_t b = std::max<size_t>(bytes, 256);
+    // a context-level cap (fd_set_workspace_limit) refuses the growth before
+    // anything is freed or allocated, exactly like a failed cudaMalloc
+    if (ctx->ws_limit && ctx->ws_bytes - e.second + b > ctx->ws_limit)
+      return set_err(ctx, FD_ERR_OOM, "workspace '%s' of %zu bytes exceeds the context's limit of %zu bytes",
+                     name, b, ctx->ws_limit);
     if (e.first) {
       // the old buffer may still be used by queued work on the stream
       FD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
       FD_CUDA(ctx, cudaFree(e.first));
+      ctx->ws_bytes -= e.second;
       e.first = nullptr;
       e.second = 0;
     }
-    size_t b = std::max<size_t>(bytes, 256);
     void* p = nullptr;
     cudaError_t err = cudaMalloc(&p, b);
+    ctx->ws_allocs++;
     if (err != cudaSuccess) {
       cudaGetLastError();
       return set_err(ctx, FD_ERR_OOM, "cudaMalloc of %zu bytes for workspace '%s' failed: %s",
@@ -47,6 +54,7 @@ fd_status workspace(fd_ctx* ctx, const char* name, size_t bytes, void** out) {
     }
     e.first = p;
     e.second = b;
+    ctx->ws_bytes += b;
   }
   *out = e.first;
   return FD_OK;
@@ -772,6 +780,20 @@ fd_status fd_set_stream(fd_ctx* ctx, void* stream) {
 const char* fd_last_error(const fd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t fd_kernel_launches(const fd_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+fd_status fd_workspace_info(const fd_ctx* ctx, size_t* bytes_held, int64_t* allocations) {
+  if (!ctx) return FD_ERR_ARG;
+  if (bytes_held) *bytes_held = ctx->ws_bytes;
+  if (allocations) *allocations = ctx->ws_allocs;
+  return FD_OK;
+}
+
+fd_status fd_set_workspace_limit(fd_ctx* ctx, size_t limit_bytes) {
+  if (!ctx) return FD_ERR_ARG;
+  ctx->err.clear();
+  ctx->ws_limit = limit_bytes;
+  return FD_OK;
+}
 
 // the per-species tables of the matrix-free Hubbard operator on A
 static fd_status build_kron(fd_ctx* ctx, fd_matrix* A, const HubbardP& p) {

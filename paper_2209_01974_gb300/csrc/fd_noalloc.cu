@@ -89,7 +89,8 @@ extern "C" fd_status fd_orthonormalize_noalloc(fd_ctx* ctx, double* V, int64_t D
       any_shift = true;
     }
     FD_TRY(tri_inverse(ctx, Rk, ns, Ri));
-    FD_TRY(rotate(ctx, V, ldv, D, ns, Ri, true));
+    // FP64 rotation in place: the tensor-core rotation needs digit workspaces
+    FD_TRY(rotate_fp64(ctx, V, ldv, D, ns, Ri, true));
     if (R) {
       FD_TRY(small_gemm_dev(ctx, Rk, R, Rt, ns));
       FD_CUDA(ctx, cudaMemcpyAsync(R, Rt, sizeof(double) * nn, cudaMemcpyDeviceToDevice, ctx->stream));

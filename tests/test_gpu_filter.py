@@ -154,3 +154,28 @@ def test_full_size_stencil_one_sweep(fd, ctx):
         got = _run_filter(fd, ctx, A, V0d, mu, alpha, beta, dt)
         tol = filter_tolerance(csr, mu, alpha, beta, V0d, u)
         assert np.all(np.abs(got - refd) <= tol)
+
+
+# windows inside the interval, touching -1 or +1, beyond it (clipped), at the
+# spectrum's edge, and a narrow one at the centre
+COEFF_WINDOWS = [(-0.3, 0.45), (-1.0, -0.6), (0.7, 1.0), (-1.5, -0.2), (0.2, 3.0),
+                 (-0.99999, -0.9999), (0.9995, 0.99999), (-0.001, 0.002)]
+
+
+@pytest.mark.parametrize("n", [2, 3, 100, 5000])
+@pytest.mark.parametrize("win", COEFF_WINDOWS)
+def test_filter_coeffs_match_oracle(fd, n, win):
+    # the library's coefficients (Sec. 2 window series, Jackson damping,
+    # p(window centre) = 1) element by element against the oracle's
+    got = fd.fd_filter_coeffs(win[0], win[1], n)
+    ref = ch.filter_coeffs(win[0], win[1], n)
+    assert got.shape == ref.shape == (n + 1,)
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_filter_coeffs_reject_bad_arguments(fd):
+    for args in [(0.1, 0.1, 10), (0.2, 0.1, 10), (-0.5, 0.5, 1), (np.nan, 0.5, 10)]:
+        with pytest.raises(fd.FDError) as e:
+            fd.fd_filter_coeffs(*args)
+        assert e.value.status == fd.FD_ERR_ARG

@@ -108,3 +108,90 @@ def test_kron_needs_original_order(fd, ctx):
         fd.fd_build_matrix(ctx, SPECS[0] + ",kron=1", C=32, sigma=64)
     with pytest.raises(fd.FDError):
         fd.fd_build_matrix(ctx, SPECS[0] + ",kron=2")
+
+
+# ---------------------------------------------------------------- full size
+RING14 = "hubbard:n_sites=14,n_up=7,n_dn=7,t=1,U=4,bc=periodic"
+D14 = 3432 * 3432
+
+
+def _ring14_entries(rows):
+    return mat._hubbard_entries(14, 7, 7, 1.0, 4.0, "periodic", rows)
+
+
+def _random_block_dev(D, nb, dtype, seed):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    return torch.randn((D, nb), dtype=dtype, device="cuda", generator=g)
+
+
+def _fetch(X):
+    import torch
+
+    def f(idx):
+        return X[torch.from_numpy(np.asarray(idx, dtype=np.int64)).cuda()].double().cpu().numpy()
+    return f
+
+
+@pytest.fixture(scope="module", params=[0, 1], ids=["stored", "kron"])
+def ring14(request, fd, ctx):
+    A = fd.fd_build_matrix(ctx, RING14 + (",kron=1" if request.param else ""))
+    assert A.D == D14
+    yield A
+    A.free()
+
+
+def _samples(seed, k):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, D14 - 1, 3431, 3432], rng.integers(0, D14, k)]))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ring14_full_size_spmmv_sampled_rows(fd, ctx, ring14, prec):
+    # the 14-site ring (11,778,624 rows) at nb = 64: 200 sampled output rows
+    # against the oracle's generated rows dotted with the gathered inputs
+    import torch
+    dt = torch.float64 if prec == "f64" else torch.float32
+    X = _random_block_dev(D14, 64, dt, 7)
+    Y = torch.empty_like(X)
+    fd.fd_spmmv(ctx, ring14, X, Y)
+    rows = _samples(3, 196)
+    r, c, v = _ring14_entries(rows)
+    import scipy.sparse as sp
+    cols = np.unique(c)
+    Aloc = sp.csr_matrix((v, (np.searchsorted(rows, r), np.searchsorted(cols, c))),
+                         shape=(len(rows), len(cols)))
+    Xc = _fetch(X)(cols)
+    exact = Aloc @ Xc
+    got = _fetch(Y)(rows)
+    u = U64 if prec == "f64" else U32
+    nnz_row = np.diff(Aloc.indptr).max()
+    assert np.all(np.abs(got - exact) <= nnz_row * u * (abs(Aloc) @ np.abs(Xc)))
+    del X, Y
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,k", [(2, 120), (4, 3)])
+def test_ring14_full_size_filter_sampled_rows(fd, ctx, ring14, prec, n, k):
+    # the fused step in the launch configuration of the bench (nb = 64, the
+    # full ring): degree 2 covers the first and second steps, degree 4 the
+    # generic step that also writes x_k; sampled rows against Alg. 2 run on
+    # their n-hop neighbourhood
+    import torch
+    from gpu_util import local_filter
+    dt = torch.float64 if prec == "f64" else torch.float32
+    lo, hi = -28.0, 56.0              # the ring's Gershgorin interval: 28 hops, U n <= 28
+    alpha, beta = ch.scale_params(lo, hi)
+    mu = ch.filter_coeffs(alpha * 9.0 + beta, alpha * 9.5 + beta, n)
+    V = _random_block_dev(D14, 64, dt, 11 + n)
+    rows = _samples(5 + n, k)
+    exact, mag = local_filter(_ring14_entries, rows, _fetch(V), mu, alpha, beta)
+    W1, W2 = torch.empty_like(V), torch.empty_like(V)
+    fd.fd_filter(ctx, ring14, V, mu, alpha, beta, W1, W2)
+    got = _fetch(V)(rows)
+    u = U64 if prec == "f64" else U32
+    g = (16 + 3) * u
+    assert np.all(np.abs(got - exact) <= (n + 1) * g * mag + (n + 2) * u * mag)
+    del V, W1, W2
+    torch.cuda.empty_cache()

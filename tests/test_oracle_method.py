@@ -23,6 +23,20 @@ def test_jackson_kernel_properties():
         assert np.all(np.diff(g) < 0) and g[-1] > 0
 
 
+def test_jackson_kernel_closed_forms():
+    # g_1 = cos(pi/(N+1)), N = n + 1; and every g_k is the normalised
+    # autocorrelation at lag k of the sine window a_v = sin(pi v/(N+1)),
+    # v = 1..N, whose squared Fourier sum is the (positive) Jackson kernel.
+    # Either fails for N off by one.
+    for n in (2, 10, 100, 501):
+        N = n + 1
+        g = ch.jackson(n)
+        assert g[1] == pytest.approx(np.cos(np.pi / (N + 1)), abs=1e-15)
+        a = np.sin(np.pi * np.arange(1, N + 1) / (N + 1))
+        ac = np.array([a[:N - k] @ a[k:] for k in range(n + 1)]) / (a @ a)
+        assert np.abs(g - ac).max() < 1e-13
+
+
 def test_window_coeffs_match_quadrature():
     x_l, x_r, n = -0.3, 0.45, 12
     c = ch.window_coeffs(x_l, x_r, n)
