@@ -374,10 +374,12 @@ def run_ozaki_probe(D=524288, ns=NS):
     return 0
 
 
-def run_kernel_only(prec, workload="stencil", nb=NB):
+def run_kernel_only(prec, workload="stencil", nb=NB, degree=12, reps=5):
     """Profiling driver: one nb-wide block of a workload matrix (the L=128 stencil by
-    default; the 14-site Hubbard ring; the 4M-node road graph), degree-12 filters in
-    FP32 or FP64; used for the ncu captures summarised under profiles/."""
+    default; the 14-site Hubbard ring, stored or matrix-free; the 4M-node road graph),
+    degree-`degree` filters in FP32 or FP64; used for the ncu captures summarised
+    under profiles/.  The matrix-free workloads read no matrix: their algorithmic
+    bytes per step are the five vector passes alone."""
     import torch
 
     import paper_2209_01974_gb300 as fd
@@ -387,7 +389,7 @@ def run_kernel_only(prec, workload="stencil", nb=NB):
     D, nnz = A.D, A.info["nnz"]
     lo, hi = fd.fd_spectral_bounds(ctx, A)
     al, be = 2 / (hi - lo), -(hi + lo) / (hi - lo)
-    mu = fd.fd_filter_coeffs(al * WINDOW[0] + be, al * WINDOW[1] + be, 12)
+    mu = fd.fd_filter_coeffs(al * WINDOW[0] + be, al * WINDOW[1] + be, degree)
     V = torch.randn((D, nb), dtype=dt, device="cuda")
     W1, W2 = torch.empty_like(V), torch.empty_like(V)
     for _ in range(2):
@@ -395,15 +397,16 @@ def run_kernel_only(prec, workload="stencil", nb=NB):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(5):
+    for _ in range(reps):
         fd.fd_filter(ctx, A, V, mu, al, be, W1, W2)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / 5 / 12
+    ms = e0.elapsed_time(e1) / reps / degree
     es = 8.0 if prec == "f64" else 4.0
+    mat_nnz = 0 if "kron=1" in KERNEL_WORKLOADS[workload] else nnz
     print(json.dumps({"kernel_only": prec, "workload": workload, "rows": D, "nnz": nnz, "nb": nb,
-                      "ms_per_step": ms,
-                      "gbs_generic_bytes": generic_step_bytes(D, nnz, nb, es) / ms / 1e6}))
+                      "degree": degree, "ms_per_step": ms,
+                      "gbs_generic_bytes": generic_step_bytes(D, mat_nnz, nb, es) / ms / 1e6}))
     return 0
 
 
@@ -567,6 +570,7 @@ def main():
                     help="profiling driver: degree-12 filters on one nb-wide block")
     ap.add_argument("--workload", choices=sorted(KERNEL_WORKLOADS), default="stencil")
     ap.add_argument("--nb", type=int, default=NB)
+    ap.add_argument("--degree", type=int, default=12, help="filter degree of --kernel-only")
     ap.add_argument("--batched", action="store_true",
                     help="batched-instances measurement (64 Anderson problems) instead of the bench")
     ap.add_argument("--instances", type=int, default=64)
@@ -595,7 +599,7 @@ def main():
     if args.kernel_only == "cholqr2":
         return run_ozaki_probe()
     if args.kernel_only:
-        return run_kernel_only(args.kernel_only, args.workload, args.nb)
+        return run_kernel_only(args.kernel_only, args.workload, args.nb, args.degree)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

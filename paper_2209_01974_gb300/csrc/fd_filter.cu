@@ -377,6 +377,10 @@ fd_status kpm_t(fd_ctx* ctx, const fd_matrix* M, int n_moments, uint64_t seed, d
 fd_status filter(fd_ctx* ctx, const fd_matrix* M, fd_prec prec, void* V, int64_t ldv, int nb,
                  int degree, const double* mu, double alpha, double beta, void* W1, void* W2,
                  int64_t ldw, double* bytes_out) {
+  // matrix-free Hubbard operator in FP32: column panels, slabs in RCM order
+  // (the FP64 step is bound by GB300's FP64 rate; it keeps the row-major kernel)
+  if (M->kron && prec == FD_F32)
+    return kron_filter(ctx, M, prec, V, ldv, nb, degree, mu, alpha, beta, W1, W2, ldw, bytes_out);
   if (prec == FD_F64)
     return filter_t<double>(ctx, M, (double*)V, ldv, nb, degree, mu, alpha, beta, (double*)W1,
                             (double*)W2, ldw, bytes_out);

@@ -60,6 +60,18 @@ struct fd_matrix {
   int32_t* kcol[2] = {nullptr, nullptr};
   double* kval[2] = {nullptr, nullptr};
   float* kval32[2] = {nullptr, nullptr};
+  // Tables of the panel kernel of the matrix-free operator (fd_kron.cu):
+  // korder: the up-spin states (slabs u) in reverse Cuthill-McKee order of the
+  // up-spin hopping graph, the order in which a step visits the slabs;
+  // kdn_ptr / kdn_ent: the down-spin hops packed as (target | sign bit << 31),
+  // the hop value being kdn_val[sign bit] (-t for +1, +t for -1)
+  int32_t* korder = nullptr;      // kdim[0]
+  uint32_t* kdn_ptr = nullptr;    // kdim[1] + 1
+  uint32_t* kdn_ent = nullptr;    // down hops
+  uint16_t* kdn_ent16 = nullptr;  // the same as (16 target | sign bit) when dim_dn <= 4096
+  double kdn_val[2] = {0, 0};
+  float kdn_val32[2] = {0, 0};
+  int kmax_up = 0;                // most up hops of one state
 };
 
 namespace fdi {
@@ -110,6 +122,13 @@ fd_status spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, const void* X,
 fd_status filter(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, void* V, int64_t ldv,
                  int nb, int degree, const double* mu, double alpha, double beta,
                  void* W1, void* W2, int64_t ldw, double* bytes_out);
+// the same filter for a matrix-free Hubbard operator: the block in 16-byte
+// column panels, slabs in korder (fd_kron.cu)
+fd_status kron_filter(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, void* V, int64_t ldv,
+                      int nb, int degree, const double* mu, double alpha, double beta,
+                      void* W1, void* W2, int64_t ldw, double* bytes_out);
+// the panel kernel's tables of A (after the per-species tables exist)
+fd_status kron_panel_tables(fd_ctx* ctx, fd_matrix* A, double t);
 // nb = 1 SpMV in SELL order, FP64: y = A x (x, y dense vectors in SELL order)
 fd_status spmv1(fd_ctx* ctx, const fd_matrix* A, const double* x, double* y);
 // KPM Chebyshev iteration with moment epilogue (fd_filter.cu)

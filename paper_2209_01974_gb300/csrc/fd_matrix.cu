@@ -833,6 +833,7 @@ static fd_status build_kron(fd_ctx* ctx, fd_matrix* A, const HubbardP& p) {
   FD_CUDA(ctx, cudaMemcpyAsync(A->kdiag, dg, sizeof(dg), cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaMemcpyAsync(A->kdiag32, dg32, sizeof(dg32), cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaStreamSynchronize(st));
+  FD_TRY(kron_panel_tables(ctx, A, p.t));
   A->kron = 1;
   return FD_OK;
 }
@@ -1031,6 +1032,7 @@ fd_status fd_matrix_free(fd_matrix* A) {
     cudaFree(A->kval[sp]); cudaFree(A->kval32[sp]);
   }
   cudaFree(A->kdiag); cudaFree(A->kdiag32);
+  cudaFree(A->korder); cudaFree(A->kdn_ptr); cudaFree(A->kdn_ent); cudaFree(A->kdn_ent16);
   delete A;
   return FD_OK;
 }

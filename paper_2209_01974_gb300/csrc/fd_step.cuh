@@ -37,6 +37,20 @@ struct V16<double> {
   __device__ __forceinline__ void st(double* p) const {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
   }
+  // loads and stores with an L2 eviction policy (createpolicy); the loads do
+  // not allocate in L1.  ldg_pol: read-only data (non-coherent path)
+  __device__ __forceinline__ void ldg_pol(const double* p, uint64_t pol) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;\n"
+        : "=d"(v[0]), "=d"(v[1]) : "l"(p), "l"(pol));
+  }
+  __device__ __forceinline__ void ld_pol(const double* p, uint64_t pol) {
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;\n"
+                 : "=d"(v[0]), "=d"(v[1]) : "l"(p), "l"(pol));
+  }
+  __device__ __forceinline__ void st_pol(double* p, uint64_t pol) const {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;\n"
+                 :: "l"(p), "d"(v[0]), "d"(v[1]), "l"(pol));
+  }
 };
 template <>
 struct V16<float> {
@@ -56,7 +70,32 @@ struct V16<float> {
   __device__ __forceinline__ void st(float* p) const {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   }
+  __device__ __forceinline__ void ldg_pol(const float* p, uint64_t pol) {
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;\n"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p), "l"(pol));
+  }
+  __device__ __forceinline__ void ld_pol(const float* p, uint64_t pol) {
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;\n"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p), "l"(pol));
+  }
+  __device__ __forceinline__ void st_pol(float* p, uint64_t pol) const {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;\n"
+                 :: "l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "l"(pol));
+  }
 };
+
+// L2 eviction policies for cache_hint accesses: the whole access range evicts
+// last (data re-read within a short window) or first (streamed once)
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
 
 template <typename T>
 struct SellArgs {
@@ -175,6 +214,11 @@ __device__ __forceinline__ void row_product(const SellArgs<T>& A, const T* __res
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+// bulk L2 prefetch of `bytes` contiguous bytes (16-byte aligned address and
+// size), issued by one thread to the copy engine; nothing waits for it
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // L2 prefetch for the rows [r0, r1) of a later CTA: the 128-byte lines of
