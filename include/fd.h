@@ -208,6 +208,18 @@ fd_status fd_spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec,
 typedef enum { FD_GEMM_AUTO = 0, FD_GEMM_FP64 = 1, FD_GEMM_OZAKI = 2 } fd_gemm_mode;
 fd_status fd_set_gemm_mode(fd_ctx* ctx, fd_gemm_mode mode);
 
+/* Debug checks (the paper has no counterpart): with on != 0, fd_filter and
+ * fd_spmmv first scan the matrix's device arrays (SELL column indices, or
+ * the matrix-free operator's hop tables) for indices outside [0, D) and
+ * return FD_ERR_BOUNDS without launching a step kernel if one is found, so a
+ * corrupted matrix is reported instead of read out of bounds.  Costs one pass
+ * over the index arrays per call.  Off by default. */
+fd_status fd_set_debug_checks(fd_ctx* ctx, int on);
+/* Test hook of the debug checks: overwrite SELL column entry `entry` (in
+ * [0, nnz_sell)) of A on the device with `col` (any value).  A matrix so
+ * changed must only be used with debug checks on.  Synchronises. */
+fd_status fd_debug_set_sell_column(fd_ctx* ctx, fd_matrix* A, int64_t entry, int32_t col);
+
 /* Diagnostic of the failure path of the tensor-core products (the paper has
  * no counterpart): launches one CTA that initialises an mbarrier nobody
  * arrives on and waits for it with the same bounded wait the products use,
@@ -293,7 +305,23 @@ typedef struct {
   double m_l, m_r;   /* window edge = target edge + m (search edge - target edge) [0.5] */
   int verbose;       /* 1: print one line per outer iteration to stderr */
   int cta_warps;     /* batched filter: warps per CTA (4 or 8) [8] */
+  int intervals;     /* target and search intervals (Sec. 2):
+                        FD_INTERVALS_RITZ: hulls of the N_t and ceil(0.75 N_s)
+                        Ritz values nearest the window centre tau;
+                        FD_INTERVALS_LEHMANN: the same search interval; each
+                        target edge moves out to the Lehmann bound at tau
+                        (fd_lehmann_bounds) for the count of wanted Ritz values
+                        on its side when that bound lies inside the search
+                        interval, so the target interval then provably holds
+                        the N_t wanted eigenvalues [FD_INTERVALS_RITZ] */
+  double lam_l, lam_r; /* inclusion interval to start from instead of the
+                        Lanczos estimate (both 0: Lanczos).  An interval that
+                        misses part of the spectrum is widened by 2 % of its
+                        width on a side whenever a Ritz value falls outside it
+                        on that side [0, 0] */
 } fd_options;
+
+enum { FD_INTERVALS_RITZ = 0, FD_INTERVALS_LEHMANN = 1 };
 
 typedef struct {
   int converged;       /* 1 if all N_t residuals <= tol */
@@ -309,11 +337,29 @@ typedef struct {
   int used_graph;      /* fd_solve_batched: 1 if the iterations ran as a CUDA graph */
 } fd_result;
 
+/* Lehmann bounds (Lehmann 1963; Sec. 2 takes the FD target and search
+ * intervals from Lehmann intervals) of the eigenvalues of H nearest the shift
+ * rho, from the search space spanned by the D x ns FP64 block V (device,
+ * leading dimension ldv, full column rank; need not be orthonormal).  With
+ * W = (H - rho) V the pencil V^T W x = mu W^T W x is solved on the device
+ * (diagonal scaling, Cholesky, Jacobi); its negative mu give
+ *   below[k] = rho + 1/mu  <=  the (k+1)-th eigenvalue below rho,
+ * its positive mu
+ *   above[k] = rho + 1/mu  >=  the (k+1)-th eigenvalue above rho,
+ * both nearest rho first.  below / above: HOST arrays of ns doubles;
+ * n_below + n_above <= ns.  V needs no alignment (it is copied into a
+ * workspace of 2 D ns doubles).  Synchronises.  Errors: FD_ERR_ARG,
+ * FD_ERR_BREAKDOWN (W numerically rank deficient, e.g. V spans an exact
+ * eigenvector with eigenvalue rho). */
+fd_status fd_lehmann_bounds(fd_ctx* ctx, const fd_matrix* A, const double* V, int64_t D, int ns,
+                            int64_t ldv, double rho, double* below, int* n_below, double* above,
+                            int* n_above);
+
 /* Filter diagonalization (Sec. 2, Alg. 1): the n_target eigenpairs of H
  * nearest the centre of the window [a, b] to residual ||H x - theta x||_2 <=
  * tol.  `degree` is the first and smallest filter degree; later degrees and
- * the target/search intervals follow the Ritz-value heuristic of fd_options
- * (the paper's Lehmann intervals are not used).
+ * the target/search intervals follow fd_options (intervals: the Ritz-value
+ * heuristic, or the paper's Lehmann intervals).
  *   theta, resid  HOST arrays of n_target doubles (ascending theta)
  *   X             optional DEVICE D x n_target FP64 row-major eigenvectors
  *                 (largest-magnitude entry positive), or NULL
@@ -322,6 +368,48 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b,
                    int n_target, int nb, int degree, double tol,
                    const fd_options* opt, fd_result* res, double* theta,
                    double* resid, double* X, int64_t ldx);
+
+/* State of an interrupted FD solve (the paper's runs last up to 26 hours,
+ * Table 6): everything the loop carries from one outer iteration to the next
+ * besides the search block itself.  Zero-initialise it to start a solve. */
+typedef struct {
+  int iteration;        /* outer iterations done (0: start from scratch) */
+  int converged;        /* 1 once the solve has converged */
+  int degree;           /* degree of the next filter */
+  int use_f32;          /* FP32 sweeps still on (FD_F32 precision form) */
+  int stall;            /* iterations in a row without halving the residual */
+  double lam_l, lam_r;  /* inclusion interval */
+  double widen;         /* its widening step */
+  double norm_h;        /* |H| estimate of the FP32 switch */
+  double window_l, window_r; /* window of the last filter */
+  double prev_max;      /* largest wanted residual of the last iteration */
+  int64_t n_spmmv, n_spmmv_f32;
+  double filter_bytes;
+  int64_t D;            /* consistency checks on resume */
+  int ns;
+  uint64_t seed;
+} fd_checkpoint;
+
+/* fd_solve in slices: starting from *ck (iteration 0: a fresh solve; else the
+ * state a previous call wrote, with the filtered search block in Vck), run at
+ * most max_iter outer iterations.  If the solve has not converged by then, it
+ * stops right after a filter application, writes the filtered D x N_s block
+ * to Vck (DEVICE, row-major, leading dimension N_s, caller-owned) and the
+ * loop's scalars to *ck, and returns FD_ERR_NOCONV with ck->converged = 0;
+ * the caller may save both (e.g. to a file) and resume later, in another
+ * process or context, with the same matrix, window, n_target, nb, degree,
+ * tol and options.  The resumed solve repeats the uninterrupted one's
+ * arithmetic exactly: the same iterations, degrees and eigenvalues.  On
+ * convergence the outputs are those of fd_solve, ck->converged = 1 and the
+ * call returns FD_OK.  Reaching opt->max_outer iterations in total returns
+ * FD_ERR_NOCONV with ck->converged = 0 and no pause.  res counts SpMMVs from
+ * the start of the solve and times for this call only.  Errors: FD_ERR_ARG
+ * also for a checkpoint whose D, N_s or seed differ from this solve's. */
+fd_status fd_solve_checkpointed(fd_ctx* ctx, const fd_matrix* A, double a, double b,
+                                int n_target, int nb, int degree, double tol,
+                                const fd_options* opt, int max_iter, fd_checkpoint* ck,
+                                double* Vck, fd_result* res, double* theta, double* resid,
+                                double* X, int64_t ldx);
 
 /* One problem of a batch: the window [a, b], the number of wanted pairs, and
  * the seed of its start block and Lanczos vector. */

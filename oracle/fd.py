@@ -11,8 +11,9 @@ Alg. 1 is printed as an image; its steps are read from Sec. 2:
   6.   choose the target and search intervals and the polynomial degree;
   8.   apply the Chebyshev filter to all N_s vectors (oracle.chebyshev).
 
-Readings where the paper is silent (the paper's Lehmann intervals are replaced
-by a Ritz-value heuristic):
+Readings where the paper is silent (intervals="ritz" replaces the paper's
+Lehmann intervals by a Ritz-value heuristic; intervals="lehmann" takes them
+from Lehmann bounds, oracle.lehmann.lehmann_intervals):
   * N_s = nb * ceil(4 N_t / nb) (Sec. 2: N_s/N_t ~ 4), at most D;
   * tau = (a + b)/2 for the window [a, b]; the N_t wanted pairs are those whose
     Ritz values are nearest tau (ties: smaller value first);
@@ -32,7 +33,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import chebyshev, lanczos, ortho, rayleigh_ritz, splitmix
+from . import chebyshev, lanczos, lehmann, ortho, rayleigh_ritz, splitmix
 from .matrices import to_scipy
 
 
@@ -61,6 +62,21 @@ def nearest_order(theta, tau):
     return np.lexsort((theta, np.abs(theta - tau)))
 
 
+def window_and_degree(target, search, alpha, beta, n_min, n_max, c_n=4.0, m_l=0.5, m_r=0.5):
+    """Filter window and degree from a target interval and a search interval
+    that contains it (step 6): window edges a fraction m of the way from the
+    target edges to the search edges; degree c_n pi / dtheta, dtheta the
+    smaller Chebyshev-angle distance between a target edge and its search
+    edge, clamped to [n_min, n_max]."""
+    (t_l, t_r), (s_l, s_r) = target, search
+    s_l, s_r = min(s_l, t_l), max(s_r, t_r)
+    th = lambda lam: math.acos(min(1.0, max(-1.0, alpha * lam + beta)))
+    dth = min(th(s_l) - th(t_l), th(t_r) - th(s_r))
+    n = n_max if dth <= 0.0 else int(math.ceil(c_n * math.pi / dth))
+    n = max(n_min, min(n_max, n))
+    return (t_l - m_l * (t_l - s_l), t_r + m_r * (s_r - t_r)), n
+
+
 def choose_filter(theta, tau, n_target, ns, alpha, beta, n_min, n_max,
                   c_n=4.0, m_l=0.5, m_r=0.5):
     """Window [w_l, w_r] and degree n from the current Ritz values (step 6)."""
@@ -69,15 +85,14 @@ def choose_filter(theta, tau, n_target, ns, alpha, beta, n_min, n_max,
     srch = theta[order[:math.ceil(0.75 * ns)]]
     t_l, t_r = tgt.min(), tgt.max()
     s_l, s_r = min(srch.min(), t_l), max(srch.max(), t_r)
-    th = lambda lam: math.acos(min(1.0, max(-1.0, alpha * lam + beta)))
-    dth = min(th(s_l) - th(t_l), th(t_r) - th(s_r))
-    n = n_max if dth <= 0.0 else int(math.ceil(c_n * math.pi / dth))
-    n = max(n_min, min(n_max, n))
-    return (t_l - m_l * (t_l - s_l), t_r + m_r * (s_r - t_r)), n, (t_l, t_r), (s_l, s_r)
+    window, n = window_and_degree((t_l, t_r), (s_l, s_r), alpha, beta, n_min, n_max, c_n, m_l, m_r)
+    return window, n, (t_l, t_r), (s_l, s_r)
 
 
 def fd_solve(csr, a, b, n_target, nb, degree, tol, ns=None, max_outer=60, seed=0,
-             lanczos_steps=20, n_max=100000, c_n=4.0, m_l=0.5, m_r=0.5):
+             lanczos_steps=20, n_max=100000, c_n=4.0, m_l=0.5, m_r=0.5, intervals="ritz"):
+    """intervals: "ritz" (hulls of the nearest Ritz values) or "lehmann" (the
+    Lehmann bounds at the shift tau, oracle.lehmann.lehmann_intervals)."""
     A = to_scipy(csr)
     D = A.shape[0]
     ns = ns or default_ns(n_target, nb, D)
@@ -107,8 +122,13 @@ def fd_solve(csr, a, b, n_target, nb, degree, tol, ns=None, max_outer=60, seed=0
             lam_r += 2 * delta
         alpha, beta = chebyshev.scale_params(lam_l, lam_r)
         if it > 0:
-            window, n, _, _ = choose_filter(theta, tau, n_target, ns, alpha, beta, degree,
-                                            n_max, c_n, m_l, m_r)
+            if intervals == "lehmann":
+                below, above = lehmann.lehmann_bounds(A, V, tau)
+                tgt, srch = lehmann.lehmann_intervals(below, above, theta, tau, n_target, ns)
+                window, n = window_and_degree(tgt, srch, alpha, beta, degree, n_max, c_n, m_l, m_r)
+            else:
+                window, n, _, _ = choose_filter(theta, tau, n_target, ns, alpha, beta, degree,
+                                                n_max, c_n, m_l, m_r)
         mu = chebyshev.filter_coeffs(alpha * window[0] + beta, alpha * window[1] + beta, n)
         V = chebyshev.cheb_filter(A, V, mu, alpha, beta)
         n_spmmv += n

@@ -35,3 +35,43 @@ def lehmann_bounds(A, V, rho):
     neg = np.sort(mu[mu < 0])          # most negative first: nearest below rho
     pos = np.sort(mu[mu > 0])[::-1]    # largest first: nearest above rho
     return rho + 1.0 / neg, rho + 1.0 / pos
+
+
+def nearest_counts(theta, tau, k):
+    """Among the k Ritz values nearest tau (ties: the smaller value first), how
+    many lie below tau and how many above it."""
+    theta = np.asarray(theta, dtype=np.float64)
+    sel = theta[np.lexsort((theta, np.abs(theta - tau)))[:k]]
+    return int(np.sum(sel < tau)), int(np.sum(sel > tau))
+
+
+def lehmann_intervals(below, above, theta, tau, n_target, ns):
+    """Target and search intervals of the FD iteration from the Ritz values and
+    the Lehmann bounds at the shift tau (the paper takes both intervals from
+    Lehmann intervals, Sec. 2, and gives no rule; this is the reading the build
+    uses).
+
+    Search interval: the hull of the ceil(0.75 ns) Ritz values nearest tau
+    (ties: smaller value first), the N_s eigenvalues the filter must keep.
+    Target interval: with k_b, k_a the numbers of the n_target nearest Ritz
+    values that lie below and above tau, each edge is the Lehmann bound
+    below[k_b - 1] (above[k_a - 1]) when that bound lies inside the search
+    interval, else the edge of the hull of the n_target nearest Ritz values.
+    By Lehmann's theorem [below[k_b - 1], above[k_a - 1]] holds at least
+    k_b + k_a eigenvalues, so once the bounds are informative the target
+    interval provably holds the n_target wanted eigenvalues, also when a
+    spurious Ritz value has taken the place of one of them; while the subspace
+    is poor the bounds lie far outside and the Ritz hull is used.  Returns
+    (target, search)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    order = np.lexsort((theta, np.abs(theta - tau)))
+    tgt = theta[order[:n_target]]
+    srch = theta[order[:int(np.ceil(0.75 * ns))]]
+    t_l, t_r = float(tgt.min()), float(tgt.max())
+    s_l, s_r = float(min(srch.min(), t_l)), float(max(srch.max(), t_r))
+    kb, ka = nearest_counts(theta, tau, n_target)
+    if 0 < kb <= len(below) and s_l < below[kb - 1] <= t_l:
+        t_l = float(below[kb - 1])
+    if 0 < ka <= len(above) and t_r <= above[ka - 1] < s_r:
+        t_r = float(above[ka - 1])
+    return (t_l, t_r), (s_l, s_r)

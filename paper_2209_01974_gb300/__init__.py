@@ -42,7 +42,18 @@ class fd_matrix_info(ctypes.Structure):
 class fd_options(ctypes.Structure):
     _fields_ = [("ns", _i32), ("max_outer", _i32), ("n_max", _i32), ("lanczos_steps", _i32),
                 ("seed", ctypes.c_uint64), ("precision", _i32), ("c_n", _dbl), ("m_l", _dbl),
-                ("m_r", _dbl), ("verbose", _i32), ("cta_warps", _i32)]
+                ("m_r", _dbl), ("verbose", _i32), ("cta_warps", _i32), ("intervals", _i32),
+                ("lam_l", _dbl), ("lam_r", _dbl)]
+
+FD_INTERVALS_RITZ, FD_INTERVALS_LEHMANN = 0, 1
+
+
+class fd_checkpoint(ctypes.Structure):
+    _fields_ = [("iteration", _i32), ("converged", _i32), ("degree", _i32), ("use_f32", _i32),
+                ("stall", _i32), ("lam_l", _dbl), ("lam_r", _dbl), ("widen", _dbl), ("norm_h", _dbl),
+                ("window_l", _dbl), ("window_r", _dbl), ("prev_max", _dbl), ("n_spmmv", _i64),
+                ("n_spmmv_f32", _i64), ("filter_bytes", _dbl), ("D", _i64), ("ns", _i32),
+                ("seed", ctypes.c_uint64)]
 
 
 class fd_problem(ctypes.Structure):
@@ -65,6 +76,8 @@ _SIGS = {
     "fd_kernel_launches": (_i64, [_vp]),
     "fd_workspace_info": (_i32, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i64)]),
     "fd_set_workspace_limit": (_i32, [_vp, ctypes.c_size_t]),
+    "fd_set_debug_checks": (_i32, [_vp, _i32]),
+    "fd_debug_set_sell_column": (_i32, [_vp, _vp, _i64, ctypes.c_int32]),
     "fd_build_matrix": (_i32, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)]),
     "fd_build_matrix_sell": (_i32, [_vp, ctypes.c_char_p, _i32, _i32, ctypes.POINTER(_vp)]),
     "fd_matrix_from_csr": (_i32, [_vp, _i64, _pi64, _pi32, _pd, _i32, _i32, ctypes.POINTER(_vp)]),
@@ -88,6 +101,9 @@ _SIGS = {
     "fd_rayleigh_ritz": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, _i64, _pd, _pd]),
     "fd_solve": (_i32, [_vp, _vp, _dbl, _dbl, _i32, _i32, _i32, _dbl, ctypes.POINTER(fd_options),
                         ctypes.POINTER(fd_result), _pd, _pd, _vp, _i64]),
+    "fd_solve_checkpointed": (_i32, [_vp, _vp, _dbl, _dbl, _i32, _i32, _i32, _dbl, ctypes.POINTER(fd_options),
+                                     _i32, ctypes.POINTER(fd_checkpoint), _vp, ctypes.POINTER(fd_result),
+                                     _pd, _pd, _vp, _i64]),
     "fd_solve_batched": (_i32, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(fd_problem), _i32,
                                 _i32, _dbl, ctypes.POINTER(fd_options), ctypes.POINTER(fd_result),
                                 _pd, _pd]),
@@ -104,6 +120,8 @@ _SIGS = {
     "fd_predict_filter_params": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_float), _pd, _pd, _pd,
                                         ctypes.POINTER(_i32)]),
     "fd_kpm_moments": (_i32, [_vp, _vp, _i32, _i32, ctypes.c_uint64, _dbl, _dbl, _pd]),
+    "fd_lehmann_bounds": (_i32, [_vp, _vp, _vp, _i64, _i32, _i64, _dbl, _pd, ctypes.POINTER(_i32), _pd,
+                                 ctypes.POINTER(_i32)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -291,6 +309,14 @@ def fd_set_workspace_limit(ctx, limit_bytes):
     _check(ctx, _lib.fd_set_workspace_limit(ctx.handle, int(limit_bytes)))
 
 
+def fd_set_debug_checks(ctx, on=True):
+    _check(ctx, _lib.fd_set_debug_checks(ctx.handle, 1 if on else 0))
+
+
+def fd_debug_set_sell_column(ctx, A, entry, col):
+    _check(ctx, _lib.fd_debug_set_sell_column(ctx.handle, A.handle, int(entry), int(col)))
+
+
 def fd_set_gemm_mode(ctx, mode):
     """mode: FD_GEMM_AUTO, FD_GEMM_FP64 or FD_GEMM_OZAKI (or 'auto'/'fp64'/'ozaki')."""
     if isinstance(mode, str):
@@ -383,6 +409,20 @@ def fd_rayleigh_ritz(ctx, A, V, AV):
     return theta, resid
 
 
+def fd_lehmann_bounds(ctx, A, V, rho):
+    """Lehmann bounds at the shift rho from the search space of the float64
+    CUDA block V: (below, above), nearest rho first."""
+    pv, ldv, D, ns, prec = _block(V, "V")
+    if prec != FD_F64:
+        raise ValueError("V must be float64")
+    below, above = np.empty(ns), np.empty(ns)
+    nb_, na_ = _i32(0), _i32(0)
+    _check(ctx, _lib.fd_lehmann_bounds(ctx.handle, A.handle, _vp(pv), D, ns, ldv, float(rho),
+                                       _dptr(below, ctypes.c_double), ctypes.byref(nb_),
+                                       _dptr(above, ctypes.c_double), ctypes.byref(na_)))
+    return below[:nb_.value].copy(), above[:na_.value].copy()
+
+
 def fd_solve(ctx, A, a, b, n_target, nb, degree, tol, X=None, raise_noconv=True, **opts):
     """Filter diagonalization; returns (theta, resid, result dict).  X: optional
     CUDA float64 tensor (D x n_target) that receives the eigenvectors."""
@@ -390,6 +430,8 @@ def fd_solve(ctx, A, a, b, n_target, nb, degree, tol, X=None, raise_noconv=True,
     for k, v in opts.items():
         if k == "precision" and isinstance(v, str):
             v = FD_F32 if v in ("f32", "fp32", "float32") else FD_F64
+        if k == "intervals" and isinstance(v, str):
+            v = {"ritz": FD_INTERVALS_RITZ, "lehmann": FD_INTERVALS_LEHMANN}[v]
         setattr(o, k, v)
     res = fd_result()
     theta = np.empty(n_target)
@@ -403,6 +445,61 @@ def fd_solve(ctx, A, a, b, n_target, nb, degree, tol, X=None, raise_noconv=True,
     if st != FD_OK and not (st == FD_ERR_NOCONV and not raise_noconv):
         _check(ctx, st)
     return theta, resid, {k: getattr(res, k) for k, _ in fd_result._fields_}
+
+
+class Checkpoint:
+    """An interrupted solve: the fd_checkpoint scalars and the filtered search
+    block (CUDA float64 tensor, D x N_s).  save/load write and read one .npz
+    file (host copies of both)."""
+
+    def __init__(self, state=None, V=None):
+        self.state = state if state is not None else fd_checkpoint()
+        self.V = V
+
+    def save(self, path):
+        fields = {k: getattr(self.state, k) for k, _ in fd_checkpoint._fields_}
+        np.savez(path, V=self.V.cpu().numpy(), **{f"s_{k}": v for k, v in fields.items()})
+
+    @classmethod
+    def load(cls, path):
+        import torch
+        z = np.load(path)
+        st = fd_checkpoint()
+        for k, _ in fd_checkpoint._fields_:
+            setattr(st, k, type(getattr(st, k))(z[f"s_{k}"].item()))
+        return cls(st, torch.from_numpy(z["V"]).cuda())
+
+
+def fd_solve_checkpointed(ctx, A, a, b, n_target, nb, degree, tol, max_iter, ckpt=None, X=None, **opts):
+    """fd_solve for at most max_iter outer iterations from the checkpoint ckpt
+    (None: a fresh solve).  Returns (theta, resid, result dict, ckpt); the
+    solve has converged when ckpt.state.converged == 1."""
+    import torch
+    o = fd_options()
+    for k, v in opts.items():
+        if k == "precision" and isinstance(v, str):
+            v = FD_F32 if v in ("f32", "fp32", "float32") else FD_F64
+        if k == "intervals" and isinstance(v, str):
+            v = {"ritz": FD_INTERVALS_RITZ, "lehmann": FD_INTERVALS_LEHMANN}[v]
+        setattr(o, k, v)
+    ns = o.ns if o.ns > 0 else nb * -(-4 * n_target // nb)
+    if ckpt is None:
+        ckpt = Checkpoint(V=torch.empty((A.D, ns), dtype=torch.float64, device="cuda"))
+    pv, ldv, _, _, _ = _block(ckpt.V, "V")
+    if ldv != ns or ckpt.V.shape[1] != ns:
+        raise ValueError("the checkpoint block must be contiguous D x N_s")
+    res = fd_result()
+    theta = np.empty(n_target)
+    resid = np.empty(n_target)
+    px, ldx = (None, 0)
+    if X is not None:
+        px, ldx, _, _, _ = _block(X, "X")
+    st = _lib.fd_solve_checkpointed(ctx.handle, A.handle, a, b, n_target, nb, degree, tol, ctypes.byref(o),
+                                    int(max_iter), ctypes.byref(ckpt.state), _vp(pv), ctypes.byref(res),
+                                    _dptr(theta, ctypes.c_double), _dptr(resid, ctypes.c_double), _vp(px), ldx)
+    if st != FD_OK and st != FD_ERR_NOCONV:
+        _check(ctx, st)
+    return theta, resid, {k: getattr(res, k) for k, _ in fd_result._fields_}, ckpt
 
 
 def fd_solve_batched(ctx, mats, problems, nb, degree, tol, raise_noconv=True, **opts):

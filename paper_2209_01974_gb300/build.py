@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfd.so")
-SOURCES = ["fd_matrix.cu", "fd_filter.cu", "fd_dense.cu", "fd_solve.cu", "fd_batched.cu", "fd_mlp.cu", "fd_ozaki.cu", "fd_noalloc.cu", "fd_comm.cu", "fd_kron.cu"]
+SOURCES = ["fd_matrix.cu", "fd_filter.cu", "fd_dense.cu", "fd_solve.cu", "fd_batched.cu", "fd_mlp.cu", "fd_ozaki.cu", "fd_noalloc.cu", "fd_comm.cu", "fd_kron.cu", "fd_lehmann.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
          "--expt-relaxed-constexpr"]

@@ -14,6 +14,7 @@
 // use evict-first (.cs) loads and stores, keeping L2 for the W1 gathers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -51,6 +52,18 @@ __global__ void __launch_bounds__(WARPS * 32, MIN_BLOCKS_F64)  // 64 registers: 
   const int64_t row0 = warp * L::RPW;
   if (row0 >= K.D) return;
   kron_rows<T, NB, MODE>(K, s, row0);
+}
+
+// debug checks: flag any index outside [0, bound) (a grid-stride scan)
+__global__ void k_scan_indices(const int32_t* idx, int64_t n, int64_t bound, int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (idx[i] < 0 || idx[i] >= bound) atomicExch(bad, 1);
+}
+__global__ void k_scan_packed(const uint32_t* ent, int64_t n, uint32_t mask, int64_t bound, int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if ((int64_t)(ent[i] & mask) >= bound) atomicExch(bad, 1);
 }
 
 // dst[i] = src[perm[i]] (to SELL order) or dst[perm[i]] = src[i] (back)
@@ -374,6 +387,37 @@ fd_status kpm_t(fd_ctx* ctx, const fd_matrix* M, int n_moments, uint64_t seed, d
 
 }  // namespace
 
+fd_status debug_check_matrix(fd_ctx* ctx, const fd_matrix* M) {
+  if (!ctx->debug_checks) return FD_OK;
+  void* p;
+  FD_TRY(workspace(ctx, "debug_flag", sizeof(int), &p));
+  int* bad = (int*)p;
+  FD_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+  const unsigned grid = (unsigned)std::max(1, ctx->num_sms * 4);
+  k_scan_indices<<<grid, 256, 0, ctx->stream>>>(M->col, M->nnz_sell, M->D, bad);
+  FD_LAUNCHED(ctx);
+  if (M->kron) {
+    for (int sp = 0; sp < 2; ++sp) {
+      int64_t nh = 0;
+      FD_CUDA(ctx, cudaMemcpyAsync(&nh, M->kptr[sp] + M->kdim[sp], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+      FD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      k_scan_indices<<<grid, 256, 0, ctx->stream>>>(M->kcol[sp], nh, M->kdim[sp], bad);
+      FD_LAUNCHED(ctx);
+      if (sp == 1 && M->kdn_ent) {
+        k_scan_packed<<<grid, 256, 0, ctx->stream>>>(M->kdn_ent, nh, 0x7fffffffu, M->kdim[1], bad);
+        FD_LAUNCHED(ctx);
+      }
+    }
+  }
+  int h = 0;
+  FD_CUDA(ctx, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  FD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h) return set_err(ctx, FD_ERR_BOUNDS, "debug check: the matrix holds an index outside [0, %lld)",
+                        (long long)M->D);
+  return FD_OK;
+}
+
 fd_status filter(fd_ctx* ctx, const fd_matrix* M, fd_prec prec, void* V, int64_t ldv, int nb,
                  int degree, const double* mu, double alpha, double beta, void* W1, void* W2,
                  int64_t ldw, double* bytes_out) {
@@ -466,6 +510,7 @@ fd_status fd_filter(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, void* V, int6
   for (int k = 0; k <= degree; ++k)
     if (!std::isfinite(mu[k])) return set_err(ctx, FD_ERR_ARG, "mu[%d] is not finite", k);
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_TRY(debug_check_matrix(ctx, A));
   return filter(ctx, A, prec, V, ldv, nb, degree, mu, alpha, beta, W1, W2, ldw, nullptr);
 }
 
@@ -481,7 +526,25 @@ fd_status fd_spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, const void* X,
     return set_err(ctx, FD_ERR_ARG, "ld must be >= nb with 16-byte aligned rows and pointers");
   if (X == Y) return set_err(ctx, FD_ERR_ARG, "X and Y must not alias");
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_TRY(debug_check_matrix(ctx, A));
   return spmmv(ctx, A, prec, X, ldx, Y, ldy, nb, true);
+}
+
+fd_status fd_set_debug_checks(fd_ctx* ctx, int on) {
+  if (!ctx) return FD_ERR_ARG;
+  ctx->err.clear();
+  ctx->debug_checks = on ? 1 : 0;
+  return FD_OK;
+}
+
+fd_status fd_debug_set_sell_column(fd_ctx* ctx, fd_matrix* A, int64_t entry, int32_t col) {
+  if (!ctx) return FD_ERR_ARG;
+  ctx->err.clear();
+  if (!A || entry < 0 || entry >= A->nnz_sell) return set_err(ctx, FD_ERR_ARG, "need a matrix and 0 <= entry < nnz_sell");
+  FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_CUDA(ctx, cudaMemcpyAsync(A->col + entry, &col, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  FD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return FD_OK;
 }
 
 fd_status fd_kpm_moments(fd_ctx* ctx, const fd_matrix* A, int n_moments, int n_random,

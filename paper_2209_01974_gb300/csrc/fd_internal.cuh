@@ -25,6 +25,7 @@ struct fd_ctx {
   size_t ws_bytes = 0;      // bytes the workspaces hold now
   int64_t ws_allocs = 0;    // cudaMalloc calls made for workspaces
   size_t ws_limit = 0;      // cap on ws_bytes (0 = none): growth beyond it fails with FD_ERR_OOM
+  int debug_checks = 0;     // scan matrix index arrays before step kernels (FD_ERR_BOUNDS)
   // pinned host staging
   void* host_stage = nullptr;
   size_t host_stage_bytes = 0;
@@ -116,6 +117,10 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 fd_status sell_from_device_csr(fd_ctx* ctx, fd_matrix* A, const int64_t* d_rowptr,
                                const int32_t* d_col, const double* d_val, int64_t nnz);
 
+// FD_ERR_BOUNDS if A's device index arrays hold an index outside [0, D)
+// (only when ctx->debug_checks; fd_filter.cu)
+fd_status debug_check_matrix(fd_ctx* ctx, const fd_matrix* A);
+
 // ---- SpMMV / Chebyshev step (fd_filter.cu) --------------------------------
 fd_status spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, const void* X,
                 int64_t ldx, void* Y, int64_t ldy, int nb, bool original_order);
@@ -181,6 +186,19 @@ fd_status copy_cols_f64_to_f32(fd_ctx* ctx, const double* src, int64_t lds, floa
                                int64_t ldd, int64_t D, int n);
 fd_status copy_cols_f32_to_f64(fd_ctx* ctx, const float* src, int64_t lds, double* dst,
                                int64_t ldd, int64_t D, int n);
+
+// ---- Lehmann bounds (fd_lehmann.cu) -----------------------------------------
+// eigenvalues (device, ascending) of the pencil A1 x = mu A2 x (A1, A2 destroyed);
+// *ok = false if A2 is not numerically positive definite
+fd_status lehmann_pencil(fd_ctx* ctx, double* A1, double* A2, int n, double* mu, bool* ok);
+// bounds rho + 1/mu: below (nearest rho first) from mu < 0, above from mu > 0
+void lehmann_from_mu(const std::vector<double>& mu, double rho, std::vector<double>* below,
+                     std::vector<double>* above);
+// Lehmann bounds at rho from Ritz vectors V, AV = A V and Ritz values theta_dev
+// (device); AV is overwritten by (A - rho) V
+fd_status lehmann_ritz(fd_ctx* ctx, const double* V, double* AV, int64_t ld, int64_t D, int ns,
+                       const double* theta_dev, double rho, std::vector<double>* below,
+                       std::vector<double>* above, bool* ok);
 
 // ---- solver pieces (fd_solve.cu) ------------------------------------------
 fd_status spectral_bounds(fd_ctx* ctx, const fd_matrix* A, int steps, uint64_t seed,

@@ -6,8 +6,8 @@
 // giving Ritz values and residuals; stop when the N_t Ritz pairs nearest the
 // target have rho <= tol; choose target/search intervals and the degree;
 // apply the Chebyshev filter }.  The paper chooses the intervals from Lehmann
-// intervals; this driver uses a Ritz-value heuristic instead (documented on
-// fd_options).  All vector work runs in the library's kernels; the host keeps
+// intervals; this driver offers those (fd_lehmann.cu) and a Ritz-value
+// heuristic (documented on fd_options).  All vector work runs in the library's kernels; the host keeps
 // only the scalar control logic (intervals, degree, the O(n) coefficients).
 #include <cuda_runtime.h>
 
@@ -281,9 +281,19 @@ fd_status fd_spectral_bounds(fd_ctx* ctx, const fd_matrix* A, int steps, uint64_
   return spectral_bounds(ctx, A, steps ? steps : 20, seed, lam_l, lam_r);
 }
 
-fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_target, int nb,
-                   int degree, double tol, const fd_options* opt_in, fd_result* res,
-                   double* theta_out, double* resid_out, double* X, int64_t ldx) {
+}  // extern "C"
+
+namespace fdi {
+
+// The FD loop.  ck == nullptr: a plain solve.  Otherwise the solve starts
+// from the checkpoint (ck->iteration > 0: the filtered block in Vck and the
+// loop's scalars), runs at most `max_iter` outer iterations and, if it has not
+// converged by then, stops right after a filter application and writes the
+// filtered block back to Vck and the scalars to ck.
+static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_target, int nb,
+                            int degree, double tol, const fd_options* opt_in, fd_result* res,
+                            double* theta_out, double* resid_out, double* X, int64_t ldx,
+                            fd_checkpoint* ck, double* Vck, int max_iter) {
   if (!ctx) return FD_ERR_ARG;
   ctx->err.clear();
   fd_options opt{};
@@ -295,6 +305,8 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_ta
     return set_err(ctx, FD_ERR_ARG, "nb must be 2, 4, ..., 128");
   if (opt.precision == FD_F32 && nb < 4) return set_err(ctx, FD_ERR_ARG, "FP32 sweeps need nb >= 4");
   if (degree < 2) return set_err(ctx, FD_ERR_ARG, "degree must be >= 2 (Alg. 2)");
+  if (opt.intervals != FD_INTERVALS_RITZ && opt.intervals != FD_INTERVALS_LEHMANN)
+    return set_err(ctx, FD_ERR_ARG, "intervals must be FD_INTERVALS_RITZ or FD_INTERVALS_LEHMANN");
   const int64_t D = A->D;
   int ns = opt.ns > 0 ? opt.ns : nb * (int)cdiv(4LL * n_target, nb);
   if (n_target < 1 || ns % nb || ns < n_target || ns > D || ns > 1024)
@@ -306,6 +318,7 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_ta
   const double c_n = opt.c_n > 0 ? opt.c_n : 4.0;
   const double m_l = opt.m_l > 0 ? opt.m_l : 0.5, m_r = opt.m_r > 0 ? opt.m_r : 0.5;
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
+  FD_TRY(debug_check_matrix(ctx, A));
   cudaStream_t st = ctx->stream;
   *res = fd_result{};
   res->ns = ns;
@@ -329,26 +342,45 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_ta
   double* rho_dev = th_dev + ns;
   int* sel_dev = (int*)(rho_dev + ns);
 
-  // steps 1-2: inclusion interval
-  tm.start();
-  double lam_l, lam_r;
-  FD_TRY(spectral_bounds(ctx, A, lsteps, opt.seed, &lam_l, &lam_r));
-  res->t_bounds = tm.stop_s();
-  const double widen = 0.01 * (lam_r - lam_l);
-  const double normH = std::max(std::fabs(lam_l), std::fabs(lam_r));
-  const double tau = 0.5 * (a + b);
-
-  k_start_block<<<(unsigned)cdiv(D * ns, 256), 256, 0, st>>>(V, ns, D, ns, fdrng::key(opt.seed, fdrng::STREAM_START));
-  FD_LAUNCHED(ctx);
-
+  const bool resume = ck && ck->iteration > 0;
+  if (ck && (ck->iteration < 0 || (resume && (ck->D != D || ck->ns != ns || ck->seed != opt.seed))))
+    return set_err(ctx, FD_ERR_ARG, "checkpoint of another problem (D, ns or seed differ)");
+  double lam_l, lam_r, widen, normH;
   double wl = a, wr = b;
   int n = degree;
   bool use_f32 = opt.precision == FD_F32;
-  std::vector<double> th(ns), rho(ns);
   double prev_max = INFINITY;
   int stall = 0;
   int it = 0;
-  bool done = false;
+  if ((opt.lam_l != 0.0 || opt.lam_r != 0.0) &&
+      !(std::isfinite(opt.lam_l) && std::isfinite(opt.lam_r) && opt.lam_l < opt.lam_r))
+    return set_err(ctx, FD_ERR_ARG, "inclusion interval override needs finite lam_l < lam_r");
+  if (!resume) {
+    // steps 1-2: inclusion interval (or the caller's)
+    tm.start();
+    if (opt.lam_l != 0.0 || opt.lam_r != 0.0) {
+      lam_l = opt.lam_l;
+      lam_r = opt.lam_r;
+    } else {
+      FD_TRY(spectral_bounds(ctx, A, lsteps, opt.seed, &lam_l, &lam_r));
+    }
+    res->t_bounds = tm.stop_s();
+    widen = 0.01 * (lam_r - lam_l);
+    normH = std::max(std::fabs(lam_l), std::fabs(lam_r));
+    k_start_block<<<(unsigned)cdiv(D * ns, 256), 256, 0, st>>>(V, ns, D, ns, fdrng::key(opt.seed, fdrng::STREAM_START));
+    FD_LAUNCHED(ctx);
+  } else {
+    lam_l = ck->lam_l; lam_r = ck->lam_r; widen = ck->widen; normH = ck->norm_h;
+    wl = ck->window_l; wr = ck->window_r; n = ck->degree;
+    use_f32 = ck->use_f32 != 0; prev_max = ck->prev_max; stall = ck->stall; it = ck->iteration;
+    res->n_spmmv = ck->n_spmmv; res->n_spmmv_f32 = ck->n_spmmv_f32; res->filter_bytes = ck->filter_bytes;
+    FD_CUDA(ctx, cudaMemcpyAsync(V, Vck, sizeof(double) * D * ns, cudaMemcpyDeviceToDevice, st));
+  }
+  const double tau = 0.5 * (a + b);
+  const int it_stop = ck ? std::min(max_outer, it + max_iter) : max_outer;
+
+  std::vector<double> th(ns), rho(ns);
+  bool done = false, paused = false;
   for (; it < max_outer; ++it) {
     tm.start();
     FD_TRY(orthonormalize(ctx, V, D, ns, ns, nullptr, nullptr));
@@ -382,11 +414,27 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_ta
     const double alpha = 2.0 / (lam_r - lam_l), beta = -(lam_r + lam_l) / (lam_r - lam_l);
     if (it > 0) {
       double t_l = INFINITY, t_r = -INFINITY, s_l = INFINITY, s_r = -INFINITY;
-      for (int i = 0; i < n_target; ++i) { t_l = std::min(t_l, th[order[i]]); t_r = std::max(t_r, th[order[i]]); }
       const int nsrch = (int)std::ceil(0.75 * ns);
+      for (int i = 0; i < n_target; ++i) { t_l = std::min(t_l, th[order[i]]); t_r = std::max(t_r, th[order[i]]); }
       for (int i = 0; i < nsrch; ++i) { s_l = std::min(s_l, th[order[i]]); s_r = std::max(s_r, th[order[i]]); }
       s_l = std::min(s_l, t_l);
       s_r = std::max(s_r, t_r);
+      if (opt.intervals == FD_INTERVALS_LEHMANN) {
+        // each target edge moves out to the Lehmann bound at tau for the count
+        // of wanted Ritz values on its side, when that bound lies inside the
+        // search interval (while the subspace is poor it lies far outside)
+        tm.start();
+        std::vector<double> below, above;
+        bool ok = false;
+        FD_TRY(lehmann_ritz(ctx, V, AV, ns, D, ns, th_dev, tau, &below, &above, &ok));
+        res->t_rr += tm.stop_s();
+        if (ok) {
+          int kb = 0, ka = 0;
+          for (int i = 0; i < n_target; ++i) { kb += th[order[i]] < tau; ka += th[order[i]] > tau; }
+          if (kb > 0 && kb <= (int)below.size() && s_l < below[kb - 1] && below[kb - 1] <= t_l) t_l = below[kb - 1];
+          if (ka > 0 && ka <= (int)above.size() && t_r <= above[ka - 1] && above[ka - 1] < s_r) t_r = above[ka - 1];
+        }
+      }
       auto ang = [&](double lam) { return std::acos(std::min(1.0, std::max(-1.0, alpha * lam + beta))); };
       const double dth = std::min(ang(s_l) - ang(t_l), ang(t_r) - ang(s_r));
       long long nn = dth <= 0.0 ? n_max : (long long)std::ceil(c_n * M_PI / dth);
@@ -410,6 +458,20 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_ta
     res->filter_bytes += bytes;
     res->n_spmmv += n;
     if (use_f32) res->n_spmmv_f32 += n;
+    if (ck && it + 1 == it_stop && it + 1 < max_outer) {  // pause after this filter application
+      ++it;
+      paused = true;
+      break;
+    }
+  }
+  if (paused) {
+    FD_CUDA(ctx, cudaMemcpyAsync(Vck, V, sizeof(double) * D * ns, cudaMemcpyDeviceToDevice, st));
+    FD_CUDA(ctx, cudaStreamSynchronize(st));
+    ck->iteration = it; ck->degree = n; ck->use_f32 = use_f32 ? 1 : 0; ck->stall = stall;
+    ck->lam_l = lam_l; ck->lam_r = lam_r; ck->widen = widen; ck->norm_h = normH;
+    ck->window_l = wl; ck->window_r = wr; ck->prev_max = prev_max;
+    ck->n_spmmv = res->n_spmmv; ck->n_spmmv_f32 = res->n_spmmv_f32; ck->filter_bytes = res->filter_bytes;
+    ck->D = D; ck->ns = ns; ck->seed = opt.seed; ck->converged = 0;
   }
   // outputs: the N_t pairs nearest tau, ascending
   std::vector<int> order = nearest_order(th, tau);
@@ -432,8 +494,36 @@ fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_ta
   res->lam_r = lam_r;
   res->window_l = wl;
   res->window_r = wr;
+  if (ck && !paused) {
+    ck->iteration = it; ck->converged = done ? 1 : 0;
+    ck->D = D; ck->ns = ns; ck->seed = opt.seed;
+  }
+  if (paused) return set_err(ctx, FD_ERR_NOCONV, "paused after %d outer iterations (checkpoint written)", it);
   if (!done) return set_err(ctx, FD_ERR_NOCONV, "no convergence after %d outer iterations", max_outer);
   return FD_OK;
+}
+
+}  // namespace fdi
+
+extern "C" {
+
+fd_status fd_solve(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_target, int nb,
+                   int degree, double tol, const fd_options* opt, fd_result* res,
+                   double* theta, double* resid, double* X, int64_t ldx) {
+  return solve_impl(ctx, A, a, b, n_target, nb, degree, tol, opt, res, theta, resid, X, ldx, nullptr,
+                    nullptr, 0);
+}
+
+fd_status fd_solve_checkpointed(fd_ctx* ctx, const fd_matrix* A, double a, double b, int n_target,
+                                int nb, int degree, double tol, const fd_options* opt, int max_iter,
+                                fd_checkpoint* ck, double* Vck, fd_result* res, double* theta,
+                                double* resid, double* X, int64_t ldx) {
+  if (!ctx) return FD_ERR_ARG;
+  ctx->err.clear();
+  if (!ck || !Vck || max_iter < 1 || ((uintptr_t)Vck & 15))
+    return set_err(ctx, FD_ERR_ARG, "need a checkpoint, an aligned device block and max_iter >= 1");
+  return solve_impl(ctx, A, a, b, n_target, nb, degree, tol, opt, res, theta, resid, X, ldx, ck, Vck,
+                    max_iter);
 }
 
 }  // extern "C"
