@@ -25,8 +25,11 @@ from Lehmann bounds, oracle.lehmann.lehmann_intervals):
     smaller Chebyshev-angle distance between a target edge and the matching
     search edge (c_n = 4 by default); n_min is the configured degree, which
     the first filter uses;
-  * a Ritz value outside [lam_l, lam_r] widens that side by 2% of the
-    interval width before the next filter.
+  * a Ritz value outside [lam_l, lam_r] moves that side out to the Ritz
+    value plus 1% of the interval width (at least 2% beyond the old edge)
+    before the next filter: outside [-1, 1] the Chebyshev polynomials grow
+    like cosh(n acosh|x|), so a side left inside the spectrum lets the filter
+    amplify the eigenvectors beyond it past what orthonormalisation can hold.
 """
 import math
 from dataclasses import dataclass, field
@@ -117,9 +120,9 @@ def fd_solve(csr, a, b, n_target, nb, degree, tol, ns=None, max_outer=60, seed=0
         if delta is None:
             delta = 0.01 * (lam_r - lam_l)
         if theta.min() < lam_l:
-            lam_l -= 2 * delta
+            lam_l = min(lam_l - 2 * delta, theta.min() - delta)
         if theta.max() > lam_r:
-            lam_r += 2 * delta
+            lam_r = max(lam_r + 2 * delta, theta.max() + delta)
         alpha, beta = chebyshev.scale_params(lam_l, lam_r)
         if it > 0:
             if intervals == "lehmann":

@@ -52,13 +52,24 @@ def cholqr_pass(V, allow_shift=True):
 
 
 def cholqr2(V):
-    """Orthonormal basis Q of span(V) and R with V = Q R (CholQR2 / shifted CholQR3)."""
+    """Orthonormal basis Q of span(V) and R with V = Q R (CholQR2 / shifted CholQR3).
+
+    The last pass factors the Gram matrix of a block that the earlier passes
+    have already orthonormalised, so its R is close to the identity.  A
+    diagonal entry off by more than a factor 4 means those passes failed (the
+    block is numerically rank deficient beyond what the shifted passes
+    recover, e.g. a filter that amplified some directions by 1e16 over the
+    rest): Breakdown, rather than a block that is not orthonormal."""
     Q = np.array(V, dtype=np.float64, copy=True)
     Rtot = np.eye(Q.shape[1])
     passes, any_shift = 0, False
+    R = None
     while passes < 2 or (any_shift and passes < 3):
         Q, R, sh = cholqr_pass(Q)
         any_shift |= sh
         Rtot = R @ Rtot
         passes += 1
+    d = np.abs(np.diag(R))
+    if not np.all((d > 0.25) & (d < 4.0)):
+        raise Breakdown("the search block is numerically rank deficient: orthonormalisation failed")
     return Q, Rtot, passes

@@ -853,8 +853,8 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
         for (int q = 0; q < nt; ++q) { theta[o + q] = th[sel[q]]; resid[o + q] = rh[sel[q]]; }
         continue;
       }
-      if (th[0] < lam_l[i]) lam_l[i] -= 2 * widen[i];
-      if (th[nsi - 1] > lam_r[i]) lam_r[i] += 2 * widen[i];
+      if (th[0] < lam_l[i]) lam_l[i] = std::min(lam_l[i] - 2 * widen[i], th[0] - widen[i]);
+      if (th[nsi - 1] > lam_r[i]) lam_r[i] = std::max(lam_r[i] + 2 * widen[i], th[nsi - 1] + widen[i]);
       const double alpha = 2.0 / (lam_r[i] - lam_l[i]), beta = -(lam_r[i] + lam_l[i]) / (lam_r[i] - lam_l[i]);
       int n = deg[i];
       if (iters[i] > 1) {

@@ -589,6 +589,23 @@ fd_status resid_norms(fd_ctx* ctx, const double* V, const double* AV, int64_t ld
   return FD_OK;
 }
 
+// The last Cholesky-QR pass factors the Gram matrix of a block the earlier
+// passes have orthonormalised: its R is close to the identity.  A diagonal
+// entry off by more than a factor 4 means they failed (a numerically rank
+// deficient block beyond what the shifted passes recover): FD_ERR_BREAKDOWN
+// instead of a block that is not orthonormal.  Synchronises.
+fd_status check_last_factor(fd_ctx* ctx, const double* Rk, int ns) {
+  std::vector<double> d(ns);
+  FD_CUDA(ctx, cudaMemcpy2DAsync(d.data(), sizeof(double), Rk, sizeof(double) * (ns + 1), sizeof(double),
+                                 ns, cudaMemcpyDeviceToHost, ctx->stream));
+  FD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < ns; ++i)
+    if (!(std::fabs(d[i]) > 0.25 && std::fabs(d[i]) < 4.0))
+      return set_err(ctx, FD_ERR_BREAKDOWN,
+                     "Cholesky-QR: the block is numerically rank deficient (last-pass R[%d][%d] = %g)", i, i, d[i]);
+  return FD_OK;
+}
+
 fd_status orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns, int64_t ldv, double* R,
                          int* passes_out) {
   void* p;
@@ -628,6 +645,7 @@ fd_status orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns, int64_t ldv,
     }
     ++passes;
   }
+  FD_TRY(check_last_factor(ctx, Rk, ns));
   if (passes_out) *passes_out = passes;
   return FD_OK;
 }

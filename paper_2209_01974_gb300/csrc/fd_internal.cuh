@@ -172,6 +172,9 @@ fd_status resid_norms(fd_ctx* ctx, const double* V, const double* AV, int64_t ld
                       int64_t D, int n, const double* theta, double* out);
 fd_status orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns, int64_t ldv,
                          double* R, int* passes);
+// FD_ERR_BREAKDOWN if the last Cholesky-QR factor's diagonal (device Rk, ns x ns)
+// is not within a factor 4 of 1 (synchronises)
+fd_status check_last_factor(fd_ctx* ctx, const double* Rk, int ns);
 fd_status rayleigh_ritz_dev(fd_ctx* ctx, const fd_matrix* A, double* V, double* AV,
                             int64_t D, int ns, int64_t ld, double* theta_dev,
                             double* resid_dev);

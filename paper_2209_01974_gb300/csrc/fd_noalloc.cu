@@ -97,6 +97,7 @@ extern "C" fd_status fd_orthonormalize_noalloc(fd_ctx* ctx, double* V, int64_t D
     }
     ++passes;
   }
+  FD_TRY(check_last_factor(ctx, Rk, ns));
   if (passes_out) *passes_out = passes;
   return FD_OK;
 }

@@ -408,9 +408,10 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
     stall = maxr > 0.5 * prev_max ? stall + 1 : 0;
     if (use_f32 && (maxr <= 100.0 * 0x1.0p-24 * normH || stall >= 2)) use_f32 = false;
     prev_max = maxr;
-    // a Ritz value outside the inclusion interval widens it
-    if (th[0] < lam_l) lam_l -= 2 * widen;
-    if (th[ns - 1] > lam_r) lam_r += 2 * widen;
+    // a Ritz value outside the inclusion interval moves that side out beyond
+    // it (outside [-1, 1] the filter grows like cosh(n acosh|x|))
+    if (th[0] < lam_l) lam_l = std::min(lam_l - 2 * widen, th[0] - widen);
+    if (th[ns - 1] > lam_r) lam_r = std::max(lam_r + 2 * widen, th[ns - 1] + widen);
     const double alpha = 2.0 / (lam_r - lam_l), beta = -(lam_r + lam_l) / (lam_r - lam_l);
     if (it > 0) {
       double t_l = INFINITY, t_r = -INFINITY, s_l = INFINITY, s_r = -INFINITY;

@@ -41,6 +41,19 @@ def test_cholqr2_orthonormal_and_matches_oracle(fd, ctx, D, ns):
     assert np.abs(Q - Qo).max() <= 1e-10
 
 
+def test_cholqr_reports_a_block_it_cannot_orthonormalise(fd, ctx):
+    # condition 1e20: the last pass's R is far from the identity -> breakdown,
+    # in both Cholesky-QR entry points (the oracle raises Breakdown likewise)
+    rng = np.random.default_rng(2)
+    U, _ = np.linalg.qr(rng.standard_normal((4000, 32)))
+    W, _ = np.linalg.qr(rng.standard_normal((32, 32)))
+    V0 = U @ np.diag(np.logspace(0, -20, 32)) @ W
+    for call in (fd.fd_orthonormalize, fd.fd_orthonormalize_noalloc):
+        with pytest.raises(fd.FDError) as e:
+            call(ctx, _t(V0))
+        assert e.value.status == fd.FD_ERR_BREAKDOWN and "rank deficient" in str(e.value)
+
+
 def test_cholqr_shifted_path_and_breakdown(fd, ctx):
     import torch
     rng = np.random.default_rng(2)

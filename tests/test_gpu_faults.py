@@ -64,12 +64,15 @@ def test_refused_digit_workspace_falls_back_to_fp64(fd):
 def test_too_narrow_inclusion_interval_is_widened(fd):
     # the 8-site chain's spectrum is [-4.2358, 20.2358]; starting from
     # [-4, 19] misses both ends: Ritz values outside widen the interval and the
-    # solve still finds the wanted eigenvalues
+    # solve still finds the wanted eigenvalues (the filter amplifies the
+    # eigenvectors outside, but the Ritz step still resolves the window)
     spec = "hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open"
     ctx = fd.fd_create(0)
     A = fd.fd_build_matrix(ctx, spec)
     lam = np.linalg.eigvalsh(mat.to_scipy(mat.build(spec)).toarray())
     th, rho, res = fd.fd_solve(ctx, A, -0.5, 0.5, 20, 32, 100, 1e-9, lam_l=-4.0, lam_r=19.0)
+    # moved out past the Ritz values found outside, which the filter has
+    # amplified until they are the extreme eigenvalues
     assert res["lam_l"] < -4.0 and res["lam_r"] > 19.0
     assert res["lam_l"] <= lam[0] and res["lam_r"] >= lam[-1]
     want = np.sort(lam[np.lexsort((lam, np.abs(lam)))[:20]])

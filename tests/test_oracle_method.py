@@ -225,3 +225,30 @@ def test_fd_config1_matches_dense_eigensolver():
     assert np.abs(r.theta - want).max() <= 1e-10 * normH
     # eigenvectors: residual certificate with the dense matrix
     assert np.abs(A @ r.X - r.X * r.theta[None, :]).max() < 1e-9
+
+
+def test_cholqr_reports_a_block_it_cannot_orthonormalise():
+    # condition 1e12: the shifted third pass recovers an orthonormal basis;
+    # condition 1e20: no pass can, and the last pass's R shows it (Breakdown
+    # instead of a basis that is not orthonormal)
+    rng = np.random.default_rng(2)
+    U, _ = np.linalg.qr(rng.standard_normal((4000, 32)))
+    W, _ = np.linalg.qr(rng.standard_normal((32, 32)))
+    Q, R, p = ortho.cholqr2(U @ np.diag(np.logspace(0, -12, 32)) @ W)
+    assert p == 3 and np.abs(Q.T @ Q - np.eye(32)).max() < 1e-13
+    with pytest.raises(ortho.Breakdown):
+        ortho.cholqr2(U @ np.diag(np.logspace(0, -20, 32)) @ W)
+
+
+def test_fd_recovers_from_an_inclusion_interval_that_misses_the_spectrum_ends(monkeypatch):
+    # [-4, 19] misses both ends of the 8-site chain's [-4.2358, 20.2358]: the
+    # filter amplifies the eigenvectors beyond, the Ritz step finds them and the
+    # interval moves out past them; the wanted eigenvalues still come out
+    csr = mat.build("hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open")
+    lam = np.linalg.eigvalsh(mat.to_scipy(csr).toarray())
+    monkeypatch.setattr(fd.lanczos, "inclusion_interval", lambda csr, m=20, seed=0: (-4.0, 19.0))
+    r = fd.fd_solve(csr, -0.5, 0.5, 20, 32, 100, 1e-9)
+    want = np.sort(lam[np.lexsort((lam, np.abs(lam)))[:20]])
+    assert r.converged and r.resid.max() <= 1e-9
+    assert r.bounds[0] <= lam[0] and r.bounds[1] >= lam[-1]
+    assert np.abs(r.theta - want).max() <= 1e-10 * np.abs(lam).max()
