@@ -50,9 +50,35 @@ WORKLOAD = {"workload": "anderson3d L=128 (2,097,152 rows) stencil, nb=64, degre
 # GB300 FP64 peak (nominal 1.25 TFLOP/s; an FMA-loop probe on this machine measured 1.20)
 FP64_TFLOPS = 1.25
 # DRAM bytes (read + write) of one generic FP32 step of this workload, from one ncu
-# capture of `bench.py --kernel-only f32` (profiles/k_cheb_step_f32_stencil_L128_nb64.md);
-# set to None whenever the step kernel changes
-TRAFFIC_F32 = 1.762259e9 + 1.027703e9
+# capture of `bench.py --kernel-only f32` (profiles/k_cheb_step_f32_stencil_L128_nb64.md),
+# with the kernel shape it was taken on and the SHA-256 of the step kernel's sources
+# at that time: when the sources differ, the figure is stale and is reported as null
+TRAFFIC_F32 = {"bytes": 1.762259e9 + 1.027703e9, "kernel": "k_cheb_step<float,64,GENERIC>",
+               "rows": 2097152, "nnz": 14680064, "nb": 64,
+               "sources_sha256": "07acd796f3c6df8ee3c9983fcae3522c5c496c4830eface00ef89088031c65fc"}
+STEP_SOURCES = ["paper_2209_01974_gb300/csrc/fd_step.cuh", "paper_2209_01974_gb300/csrc/fd_filter.cu"]
+
+
+def step_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in STEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_record(D, nnz, nb):
+    """The captured DRAM bytes per launch if they belong to this kernel shape and
+    to the step kernel's current sources, else None with the reason."""
+    t = TRAFFIC_F32
+    if (t["rows"], t["nnz"], t["nb"]) != (D, nnz, nb):
+        return None, "traffic captured on another shape"
+    if t["sources_sha256"] != step_sources_sha256():
+        print("bench: roofline.traffic is stale (the step kernel's sources changed since the ncu "
+              "capture); reporting null", file=sys.stderr)
+        return None, "step kernel changed since the ncu capture"
+    return t["bytes"], f"ncu dram__bytes_read.sum + dram__bytes_write.sum of {t['kernel']}, one launch"
 
 
 def filter_bytes(D, nnz, nb, n, Sx):
@@ -332,8 +358,8 @@ def run_gpu(args):
     filt_ms = sum(t[0] for t in times)
     achieved = sweep_bytes32 * args.steps / (filt_ms * 1e-3) / 1e9
 
-    # all-FP64 form of the same step: FP64-ALU bound on GB300
-    k64 = max(1, min(2, args.steps))
+    # all-FP64 form of the same step (FP64-ALU bound on GB300), over as many steps
+    k64 = args.steps
     total64, times64, _, _ = timed("f64", k64, 1)
     filt64 = sum(t[0] for t in times64)
     flops64 = (NS // NB) * DEGREE * (2.0 * nnz * NB + 6.0 * NB * D)
@@ -361,13 +387,17 @@ def run_gpu(args):
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_val = world * sweep_bytes32 / (statistics.mean(e2e_ms) * 1e-3) / 1e9
 
-    # time to solution: 20 eigenpairs of the 8-site Hubbard chain at residual <= 1e-9
+    # time to solution: 20 eigenpairs of the 8-site Hubbard chain (config 1), and
+    # 32 eigenpairs of the L = 48, W = 16 Anderson model in every form
     A1 = fd.fd_build_matrix(ctx, "hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open")
     tts = {}
     for prec in ("f64", "f32"):
         th, rho, res = fd.fd_solve(ctx, A1, -0.5, 0.5, 20, 32, 100, 1e-9, precision=prec)
         tts[prec] = {"seconds": res["t_total"], "iterations": res["iterations"],
                      "n_spmmv": res["n_spmmv"], "max_resid": float(rho.max())}
+    A1.free()
+    tts48 = {} if args.no_tts else time_to_solution(ctx, args.tts_forms_bench.split(","))
+    c3 = {} if args.no_config3 else config3_sweep(ctx)
 
     peaks = {}
     try:
@@ -389,6 +419,7 @@ def run_gpu(args):
                "sample": f"oracle Alg. 2 filter (scipy CSR SpMMV), degree 3 on one 64-wide block of the "
                          f"L=128 stencil, columns split over {cores} spawned processes: {dt:.2f} s",
                "one_core": {"value": gbs1, "unit": UNIT, "seconds": dt1}}
+    traffic, traffic_note = traffic_record(D, nnz, NB)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -396,7 +427,8 @@ def run_gpu(args):
                 "dtype_detail": "FP32 filter sweeps; FP64 Cholesky-QR, Rayleigh-Ritz, residuals",
                 "data": "synthetic", "config": WORKLOAD,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": TRAFFIC_F32, "peak_source": peak_note,
+                             "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_note,
+                             "peak_source": peak_note,
                              "kernel": "k_cheb_step<float,64> (fused SpMMV + recurrence + "
                                        "accumulation), averaged over the filter phase",
                              "bytes_per_generic_launch": generic_step_bytes(D, nnz, NB, 4.0)},
@@ -409,11 +441,90 @@ def run_gpu(args):
                 "phases_ms_per_step": {"filter": filt_ms / args.steps,
                                        "ortho_rr": sum(t[1] - t[0] for t in times) / args.steps},
                 "time_to_solution": {"workload": "hubbard 8 sites 4+4 open, 20 eigenpairs nearest "
-                                                 "[-0.5,0.5], nb=32, degree>=100, tol 1e-9", **tts}}
+                                                 "[-0.5,0.5], nb=32, degree>=100, tol 1e-9", **tts},
+                "time_to_solution_anderson48": tts48,
+                "config3_hubbard14": c3}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+TTS_SPEC = "anderson3d:L=48,W=16,seed=3"
+TTS_FORMS = {"f64": ("f64", False, "ritz"), "f64_lehmann": ("f64", False, "lehmann"),
+             "f32": ("f32", False, "ritz"), "f32_lehmann": ("f32", False, "lehmann"),
+             "f64_learned": ("f64", True, "ritz"), "f32_learned": ("f32", True, "ritz"),
+             "f32_learned_lehmann": ("f32", True, "lehmann")}
+
+
+def time_to_solution(ctx, forms, spec=TTS_SPEC, nt=32, nb=32, half_width=0.002, max_outer=40,
+                     n_max=100000):
+    """Time to nt eigenpairs at residual <= 1e-9 of the L = 48, W = 16 Anderson
+    model (110,592 rows) nearest 0, per form: plain FP64 (Ritz or Lehmann
+    intervals), FP32 sweeps with an FP64 finish, and the learned filter
+    parameters; eigenvalues compared with the first form's."""
+    import paper_2209_01974_gb300 as fd
+    from paper_2209_01974_gb300 import predictor
+    A = fd.fd_build_matrix(ctx, spec)
+    params = predictor.load()
+    out = {"workload": f"{spec} ({A.D} rows), {nt} eigenpairs nearest 0 (window +-{half_width}), "
+                       f"nb={nb}, degree >= 100, tol 1e-9, max_outer {max_outer}, n_max {n_max}"}
+    ref = None
+    for name in forms:
+        prec, learned, iv = TTS_FORMS[name]
+        th, rho, res, pred = predictor.solve_with(ctx, params if learned else None, A, -half_width, half_width,
+                                                  nt, nb, 100, 1e-9, seed=0, precision=prec,
+                                                  max_outer=max_outer, n_max=n_max, intervals=iv)
+        th = np.sort(th)
+        if ref is None and res["converged"]:
+            ref = th
+        out[name] = {"converged": res["converged"], "seconds": res["t_total"], "iterations": res["iterations"],
+                     "n_spmmv": res["n_spmmv"], "n_spmmv_f32": res["n_spmmv_f32"],
+                     "final_degree": res["final_degree"], "max_resid": float(rho.max()),
+                     "max_abs_dtheta_vs_first_converged": (float(np.abs(th - ref).max())
+                                                           if ref is not None and res["converged"] else None),
+                     "params": pred}
+    A.free()
+    return out
+
+
+def config3_sweep(ctx, degree=50, reps=3):
+    """The 14-site Hubbard ring (11,778,624 rows) fused step at nb = 32, 64, 128:
+    the matrix-free operator in FP32 and FP64, and the stored matrix in FP32;
+    per-step time of degree-`degree` filters and the step's algorithmic GB/s."""
+    import torch
+
+    import paper_2209_01974_gb300 as fd
+    out = {"workload": "hubbard ring 14 sites 7+7 periodic, degree-50 filters on one nb-wide block"}
+    peak = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs")
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None) or 6800.0
+    for label, spec, cases in (("kron", KERNEL_WORKLOADS["hubbard14kron"], [("f32", 32), ("f32", 64),
+                                                                          ("f32", 128), ("f64", 64)]),
+                               ("stored", KERNEL_WORKLOADS["hubbard14"], [("f32", 64)])):
+        A = fd.fd_build_matrix(ctx, spec)
+        D, nnz = A.D, A.info["nnz"]
+        lo, hi = fd.fd_spectral_bounds(ctx, A)
+        al, be = 2 / (hi - lo), -(hi + lo) / (hi - lo)
+        mu = fd.fd_filter_coeffs(al * 9.0 + be, al * 9.5 + be, degree)
+        for prec, nb in cases:
+            dt = torch.float64 if prec == "f64" else torch.float32
+            es = 8.0 if prec == "f64" else 4.0
+            V = torch.randn((D, nb), dtype=dt, device="cuda")
+            W1, W2 = torch.empty_like(V), torch.empty_like(V)
+            fd.fd_filter(ctx, A, V, mu, al, be, W1, W2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fd.fd_filter(ctx, A, V, mu, al, be, W1, W2)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps / degree
+            gbs = generic_step_bytes(D, 0 if label == "kron" else nnz, nb, es) / ms / 1e6
+            out[f"{label}_{prec}_nb{nb}"] = {"ms_per_step": ms, "gbs": gbs, "frac_of_measured_peak": gbs / peak}
+            del V, W1, W2
+            torch.cuda.empty_cache()
+        A.free()
+    return out
 
 
 KERNEL_WORKLOADS = {
@@ -607,39 +718,14 @@ def run_chi(args):
 
 
 def run_tts(args):
-    """Time to N_t eigenpairs at residual <= 1e-9 on a mid-size matrix, for the
-    forms named in --tts-forms: plain FP64 (heuristic interval and degree), FP32
-    sweeps with an FP64 finish (heuristic), and either precision with the trained
-    filter-parameter predictor.  Each form's eigenvalues are compared with the
-    first form's."""
+    """Time to N_t eigenpairs at residual <= 1e-9 of a mid-size matrix for the
+    forms named in --tts-forms (see time_to_solution)."""
     import paper_2209_01974_gb300 as fd
-    from paper_2209_01974_gb300 import predictor
     ctx = fd.fd_create(0)
-    A = fd.fd_build_matrix(ctx, args.tts_spec)
-    a, b = -args.tts_half_width, args.tts_half_width
-    nt, nb = args.tts_nt, args.nb if args.nb != NB else 32
-    params = predictor.load()
-    out = {}
-    ref = None
-    forms = {"f64": ("f64", None, "ritz"), "f32": ("f32", None, "ritz"),
-             "f64_learned": ("f64", params, "ritz"), "f32_learned": ("f32", params, "ritz"),
-             "f64_lehmann": ("f64", None, "lehmann"), "f32_lehmann": ("f32", None, "lehmann"),
-             "f32_learned_lehmann": ("f32", params, "lehmann")}
-    for name in args.tts_forms.split(","):
-        prec, p, iv = forms[name]
-        th, rho, res, pred = predictor.solve_with(ctx, p, A, a, b, nt, nb, 100, 1e-9, seed=0, precision=prec,
-                                                  max_outer=args.max_outer, n_max=args.n_max,
-                                                  intervals=iv)
-        if ref is None:
-            ref = np.sort(th)
-        out[name] = {"converged": res["converged"], "seconds": res["t_total"],
-                     "iterations": res["iterations"], "n_spmmv": res["n_spmmv"],
-                     "n_spmmv_f32": res["n_spmmv_f32"], "final_degree": res["final_degree"],
-                     "max_resid": float(rho.max()),
-                     "max_abs_dtheta_vs_first": float(np.abs(np.sort(th) - ref).max()),
-                     "params": pred}
-    print(json.dumps({"tts_workload": f"{args.tts_spec} ({A.D} rows), {nt} eigenpairs nearest the "
-                                      f"centre of [{a}, {b}], nb={nb}, degree >= 100, tol 1e-9", **out}))
+    out = time_to_solution(ctx, args.tts_forms.split(","), spec=args.tts_spec, nt=args.tts_nt,
+                           nb=args.nb if args.nb != NB else 32, half_width=args.tts_half_width,
+                           max_outer=args.max_outer, n_max=args.n_max)
+    print(json.dumps({"tts": out}))
     return 0
 
 
@@ -659,7 +745,7 @@ def main():
                     help="batched-instances measurement (64 Anderson problems) instead of the bench")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--max-outer", type=int, default=40)
-    ap.add_argument("--n-max", type=int, default=20000)
+    ap.add_argument("--n-max", type=int, default=100000)
     ap.add_argument("--learned-eval", action="store_true",
                     help="predictor vs heuristic on the road-like graph Laplacian")
     ap.add_argument("--side", type=int, default=400)
@@ -671,6 +757,10 @@ def main():
     ap.add_argument("--tts-nt", type=int, default=32)
     ap.add_argument("--tts-half-width", type=float, default=0.002)
     ap.add_argument("--tts-forms", default="f64,f32,f32_learned")
+    ap.add_argument("--tts-forms-bench", default="f64,f64_lehmann,f32,f32_learned",
+                    help="forms of the time-to-solution block of the default bench line")
+    ap.add_argument("--no-tts", action="store_true", help="skip the L=48 time-to-solution block")
+    ap.add_argument("--no-config3", action="store_true", help="skip the 14-site Hubbard ring sweep")
     args = ap.parse_args()
     if args.chi:
         return run_chi(args)
