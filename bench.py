@@ -606,12 +606,14 @@ def run_batched(args):
     """64 independent 3D Anderson instances (L = 16 + floor(33 u), W = 2 + 14 u from
     SplitMix64 streams 5 / 6, seeds 0..63), 16 eigenpairs nearest E = 0, nb = 16,
     degree >= 200, residual <= 1e-9: one batched solve (persistent filter launch
-    per outer iteration, CUDA graph, autotuned nb / C / CTA shape) against 64
-    sequential fd_solve calls."""
+    per outer iteration, CUDA graph, autotuned nb / C / CTA shape) against the same
+    instances solved one by one, in the precision form --precision, with each
+    instance's learned filter constants when --learned."""
     import torch
 
     import paper_2209_01974_gb300 as fd
     from fd_inputs import anderson_instance
+    from paper_2209_01974_gb300 import predictor
     n = args.instances
     specs = []
     for s in range(n):
@@ -622,30 +624,51 @@ def run_batched(args):
     tune = fd.fd_tune_batched(ctx, specs, 16, 20)
     t_tune = time.perf_counter() - t0
     mats = [fd.fd_build_matrix(ctx, sp, C=tune["C"]) for sp in specs]
-    probs = [(-0.01, 0.01, 16, s) for s in range(n)]
+    nb = tune["nb"]
+    ns = nb * -(-64 // nb)
+    probs, preds = [], []
+    params = predictor.load() if args.learned else None
+    for s, m in enumerate(mats):
+        p = {"c_n": 0.0, "m_l": 0.0, "m_r": 0.0}
+        if params is not None:
+            f = fd.fd_filter_features(ctx, m, -0.01, 0.01, 16, nb, ns, s)
+            p = fd.fd_predict_filter_params(ctx, params, f)
+        preds.append(p)
+        probs.append((-0.01, 0.01, 16, s, p["c_n"], p["m_l"], p["m_r"]))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out, res = fd.fd_solve_batched(ctx, mats, probs, tune["nb"], 200, 1e-9, raise_noconv=False,
+    out, res = fd.fd_solve_batched(ctx, mats, probs, nb, 200, 1e-9, raise_noconv=False,
                                    cta_warps=tune["cta_warps"], max_outer=args.max_outer,
-                                   n_max=args.n_max)
+                                   n_max=args.n_max, precision=args.precision)
     t_batched = time.perf_counter() - t0
     t0 = time.perf_counter()
-    seq = []
-    for m, (a, b, nt, sd) in zip(mats, probs):
-        th, rho, r = fd.fd_solve(ctx, m, a, b, nt, tune["nb"], 200, 1e-9, seed=sd, raise_noconv=False,
-                                 max_outer=args.max_outer, n_max=args.n_max)
+    seq, seq_th = [], []
+    for m, (a, b, nt, sd, cn, ml, mr) in zip(mats, probs):
+        extra = {"c_n": cn, "m_l": ml, "m_r": mr} if params is not None else {}
+        th, rho, r = fd.fd_solve(ctx, m, a, b, nt, nb, 200, 1e-9, seed=sd, raise_noconv=False,
+                                 max_outer=args.max_outer, n_max=args.n_max, precision=args.precision,
+                                 **extra)
         seq.append(r)
+        seq_th.append(th)
     t_seq = time.perf_counter() - t0
+    both = [i for i in range(n) if res[i]["converged"] and seq[i]["converged"]]
+    dth = max((float(np.abs(out[i][0] - seq_th[i]).max()) for i in both), default=None)
     rows = sum(m.D for m in mats)
-    line = {"workload": f"batched: {n} Anderson instances L 16..48, W 2..16, 16 pairs at E=0, "
-                        "nb from tuner, degree >= 200, tol 1e-9",
+    line = {"workload": f"batched: {n} Anderson instances L 16..48, W 2..16, 16 pairs at E=0 (window "
+                        "+-0.01), nb from tuner, degree >= 200, tol 1e-9",
+            "precision": args.precision, "learned": bool(args.learned),
+            "max_outer": args.max_outer, "n_max": args.n_max,
             "rows_total": rows, "tuner": tune, "tuner_seconds": t_tune,
             "batched_seconds": t_batched, "sequential_seconds": t_seq,
             "speedup": t_seq / t_batched,
             "converged_batched": sum(r["converged"] for r in res),
             "converged_sequential": sum(r["converged"] for r in seq),
+            "n_spmmv_batched": int(sum(r["n_spmmv"] for r in res)),
+            "n_spmmv_f32_batched": int(sum(r["n_spmmv_f32"] for r in res)),
             "used_graph": res[0]["used_graph"],
-            "max_resid_batched": float(max((o[1].max() for o in out), default=0.0))}
+            "max_abs_dtheta_batched_vs_sequential": dth,
+            "max_resid_batched": float(max((o[1][np.isfinite(o[1])].max() for o in out
+                                             if np.isfinite(o[1]).any()), default=0.0))}
     print(json.dumps(line))
     return 0
 
@@ -744,6 +767,9 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="batched-instances measurement (64 Anderson problems) instead of the bench")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
+                    help="precision form of --batched")
+    ap.add_argument("--learned", action="store_true", help="--batched: each instance's learned constants")
     ap.add_argument("--max-outer", type=int, default=40)
     ap.add_argument("--n-max", type=int, default=100000)
     ap.add_argument("--learned-eval", action="store_true",

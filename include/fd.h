@@ -411,12 +411,15 @@ fd_status fd_solve_checkpointed(fd_ctx* ctx, const fd_matrix* A, double a, doubl
                                 double* Vck, fd_result* res, double* theta, double* resid,
                                 double* X, int64_t ldx);
 
-/* One problem of a batch: the window [a, b], the number of wanted pairs, and
- * the seed of its start block and Lanczos vector. */
+/* One problem of a batch: the window [a, b], the number of wanted pairs, the
+ * seed of its start block and Lanczos vector, and optional per-instance
+ * interval constants. */
 typedef struct {
   double a, b;
   int n_target;
   uint64_t seed;
+  double c_n, m_l, m_r; /* this instance's degree constant and window margins
+                           (0: fd_options' values), e.g. the learned ones */
 } fd_problem;
 
 /* Filter diagonalization of n_inst independent problems at once (Alg. 1 per

@@ -57,7 +57,8 @@ class fd_checkpoint(ctypes.Structure):
 
 
 class fd_problem(ctypes.Structure):
-    _fields_ = [("a", _dbl), ("b", _dbl), ("n_target", _i32), ("seed", ctypes.c_uint64)]
+    _fields_ = [("a", _dbl), ("b", _dbl), ("n_target", _i32), ("seed", ctypes.c_uint64),
+                ("c_n", _dbl), ("m_l", _dbl), ("m_r", _dbl)]
 
 
 class fd_result(ctypes.Structure):
@@ -409,6 +410,19 @@ def fd_rayleigh_ritz(ctx, A, V, AV):
     return theta, resid
 
 
+def _options(opts):
+    """fd_options from keyword arguments ('f32'/'f64' precision and
+    'ritz'/'lehmann' intervals accepted as strings)."""
+    o = fd_options()
+    for k, v in opts.items():
+        if k == "precision" and isinstance(v, str):
+            v = FD_F32 if v in ("f32", "fp32", "float32") else FD_F64
+        if k == "intervals" and isinstance(v, str):
+            v = {"ritz": FD_INTERVALS_RITZ, "lehmann": FD_INTERVALS_LEHMANN}[v]
+        setattr(o, k, v)
+    return o
+
+
 def fd_lehmann_bounds(ctx, A, V, rho):
     """Lehmann bounds at the shift rho from the search space of the float64
     CUDA block V: (below, above), nearest rho first."""
@@ -426,13 +440,7 @@ def fd_lehmann_bounds(ctx, A, V, rho):
 def fd_solve(ctx, A, a, b, n_target, nb, degree, tol, X=None, raise_noconv=True, **opts):
     """Filter diagonalization; returns (theta, resid, result dict).  X: optional
     CUDA float64 tensor (D x n_target) that receives the eigenvectors."""
-    o = fd_options()
-    for k, v in opts.items():
-        if k == "precision" and isinstance(v, str):
-            v = FD_F32 if v in ("f32", "fp32", "float32") else FD_F64
-        if k == "intervals" and isinstance(v, str):
-            v = {"ritz": FD_INTERVALS_RITZ, "lehmann": FD_INTERVALS_LEHMANN}[v]
-        setattr(o, k, v)
+    o = _options(opts)
     res = fd_result()
     theta = np.empty(n_target)
     resid = np.empty(n_target)
@@ -475,13 +483,7 @@ def fd_solve_checkpointed(ctx, A, a, b, n_target, nb, degree, tol, max_iter, ckp
     (None: a fresh solve).  Returns (theta, resid, result dict, ckpt); the
     solve has converged when ckpt.state.converged == 1."""
     import torch
-    o = fd_options()
-    for k, v in opts.items():
-        if k == "precision" and isinstance(v, str):
-            v = FD_F32 if v in ("f32", "fp32", "float32") else FD_F64
-        if k == "intervals" and isinstance(v, str):
-            v = {"ritz": FD_INTERVALS_RITZ, "lehmann": FD_INTERVALS_LEHMANN}[v]
-        setattr(o, k, v)
+    o = _options(opts)
     ns = o.ns if o.ns > 0 else nb * -(-4 * n_target // nb)
     if ckpt is None:
         ckpt = Checkpoint(V=torch.empty((A.D, ns), dtype=torch.float64, device="cuda"))
@@ -503,14 +505,12 @@ def fd_solve_checkpointed(ctx, A, a, b, n_target, nb, degree, tol, max_iter, ckp
 
 
 def fd_solve_batched(ctx, mats, problems, nb, degree, tol, raise_noconv=True, **opts):
-    """problems: list of (a, b, n_target, seed).  Returns (list of (theta, resid),
-    list of result dicts)."""
+    """problems: list of (a, b, n_target, seed) or (a, b, n_target, seed, c_n, m_l,
+    m_r).  Returns (list of (theta, resid), list of result dicts)."""
     n = len(mats)
     arr = (_vp * n)(*[m.handle for m in mats])
-    pr = (fd_problem * n)(*[fd_problem(a, b, nt, sd) for (a, b, nt, sd) in problems])
-    o = fd_options()
-    for k, v in opts.items():
-        setattr(o, k, v)
+    pr = (fd_problem * n)(*[fd_problem(*p) for p in problems])
+    o = _options(opts)
     res = (fd_result * n)()
     tot = sum(p[2] for p in problems)
     theta = np.empty(tot)

@@ -33,7 +33,10 @@ constexpr int BMAX_NS = 96;  // single-CTA shared-memory Jacobi / Cholesky limit
 
 struct BInst {
   SellArgs<double> A;
+  SellArgs<float> A32;  // the same SELL arrays with the FP32 values
   double* V;      // D x ns, ld = ns
+  float* V32;     // FP32 copy of V for FP32 sweeps (nullptr unless the FP32 form is on)
+  float* W32;     // (ns / nb) bundles x 2 x D x nb
   double* AV;     // D x ns
   double* W;      // (ns / nb) bundles x 2 x D x nb
   double* G;      // ns x ns (Gram / Rayleigh quotient)
@@ -53,6 +56,8 @@ struct BParams {  // rewritten by the host before every outer iteration
   int mu_off;     // offset of mu_0 in the coefficient table
   int flags;      // device-written: 1 = a Cholesky pass was shifted, 2 = breakdown
   double alpha, beta;
+  int f32;        // 1: this iteration's filter runs in FP32 (V32, W32, FP32 values)
+  int pad;
 };
 
 struct BTask {
@@ -118,6 +123,43 @@ __device__ __forceinline__ void batched_row_group(const BatchArgs& b, int t, int
   }
 }
 
+// FP32 sweeps of an instance in the FP32 form: the same steps on V32, W32 and
+// the FP32 matrix values (FP32 accumulation), as fd_solve's FP32 sweeps
+template <int NB>
+__device__ __forceinline__ void batched_row_group_f32(const BatchArgs& b, int t, int64_t lrow0, int k) {
+  const BTask tk = b.task[t];
+  const BInst& I = b.inst[tk.inst];
+  const BParams& P = b.par[tk.inst];
+  const int64_t D = I.A.D;
+  const int n = P.degree;
+  if (!P.active || k > n) return;
+  float* V = I.V32 + (int64_t)tk.bundle * NB;
+  float* W1 = I.W32 + (int64_t)tk.bundle * 2 * D * NB;
+  float* W2 = W1 + D * NB;
+  const double* mu = b.mu + P.mu_off;
+  StepArgs<float> s{};
+  if (k == 1) {
+    s.X = V; s.ldx = I.ns; s.Y = W1; s.ldy = NB;
+    s.c_ax = (float)P.alpha; s.c_x = (float)P.beta;
+    cheb_rows<float, NB, MODE_SPMMV>(I.A32, s, lrow0);
+  } else if (k == 2) {
+    s.X = W1; s.ldx = NB; s.Z = V; s.ldz = I.ns;
+    s.Y = n > 2 ? W2 : nullptr; s.ldy = NB;
+    s.Vout = V; s.ldvo = I.ns;
+    s.c_ax = (float)(2 * P.alpha); s.c_x = (float)(2 * P.beta);
+    s.mu0 = (float)mu[0]; s.mu1 = (float)mu[1]; s.mu2 = (float)mu[2];
+    cheb_rows<float, NB, MODE_SECOND>(I.A32, s, lrow0);
+  } else {
+    float* X = (k & 1) ? W2 : W1;
+    float* Z = (k & 1) ? W1 : W2;
+    s.X = X; s.ldx = NB; s.Z = Z; s.ldz = NB;
+    s.Y = k < n ? Z : nullptr; s.ldy = NB;
+    s.Vin = V; s.ldvi = I.ns; s.Vout = V; s.ldvo = I.ns;
+    s.c_ax = (float)(2 * P.alpha); s.c_x = (float)(2 * P.beta); s.mu2 = (float)mu[k];
+    cheb_rows<float, NB, MODE_GENERIC>(I.A32, s, lrow0);
+  }
+}
+
 template <int NB>
 __global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
   using L = Layout<double, NB>;
@@ -140,9 +182,33 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
         if (s_off[mid] <= r0) lo = mid; else hi = mid - 1;
       }
       const int64_t lrow0 = r0 - s_off[lo];
-      if (lrow0 < b.inst[b.task[lo].inst].A.D) batched_row_group<NB>(b, lo, lrow0, k);
+      const int inst = b.task[lo].inst;
+      if (lrow0 >= b.inst[inst].A.D) continue;
+      if constexpr (NB >= 4) {
+        // an FP32 warp covers twice the rows of an FP64 one (16-byte vectors hold
+        // four floats): FP32 tasks take the even FP64 row groups (task rows are
+        // padded to the FP32 granule when the FP32 form is on)
+        if (!b.spmmv_only && b.par[inst].f32) {
+          if (((lrow0 / L::RPW) & 1) == 0) batched_row_group_f32<NB>(b, lo, lrow0, k);
+          continue;
+        }
+      }
+      batched_row_group<NB>(b, lo, lrow0, k);
     }
     if (!b.spmmv_only) grid.sync();
+  }
+}
+
+// V32 <- (float) V before an FP32 filter, V <- (double) V32 after it, for the
+// instances whose filter runs in FP32 this iteration (blockIdx.y = instance)
+__global__ void k_bconvert(const BInst* insts, const BParams* par, int to32) {
+  const BInst& I = insts[blockIdx.y];
+  const BParams& P = par[blockIdx.y];
+  if (!P.active || !P.f32 || P.degree == 0 || !I.V32) return;
+  const int64_t n = I.A.D * I.ns;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    if (to32) I.V32[e] = (float)I.V[e];
+    else I.V[e] = (double)I.V32[e];
   }
 }
 
@@ -473,6 +539,7 @@ __global__ void k_bstart(double* V, int64_t n, uint64_t key) {
 // ---------------------------------------------------------------------------
 struct Batch {
   int n = 0, nb = 0, warps = WARPS, ns_max = 0;
+  bool f32 = false;  // FP32 sweeps available (the FP32 form)
   std::vector<BInst> h_inst;
   std::vector<BTask> h_task;
   std::vector<int64_t> h_off;
@@ -520,11 +587,13 @@ const void* filter_kernel_for(int nb) {
 }
 
 fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, const int* ns,
-                      int nb, int warps, size_t mu_cap) {
+                      int nb, int warps, size_t mu_cap, bool f32 = false) {
   B.n = n;
   B.nb = nb;
   B.warps = warps;
-  const int rpw = 32 / std::min(32, nb * 8 / 16);
+  B.f32 = f32;
+  // rows per warp of the FP64 step; the FP32 step covers twice as many
+  const int rpw = (32 / std::min(32, nb * 8 / 16)) * (f32 ? 2 : 1);
   // arena layout per instance
   size_t bytes = 0;
   std::vector<size_t> off(n);
@@ -534,6 +603,8 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
     off[i] = bytes;
     bytes += sizeof(double) * (2 * D * ns[i] + 2 * D * ns[i] + 3 * nn + GSLICES * nn + 2 * ns[i] +
                                RBLK * ns[i]);
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (f32) bytes += sizeof(float) * 3 * D * ns[i] + 256;  // V32 and the bundles' W32
     bytes = (bytes + 255) & ~(size_t)255;
     B.ns_max = std::max(B.ns_max, ns[i]);
     B.max_D = std::max<int64_t>(B.max_D, D);
@@ -545,6 +616,8 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
     BInst& I = B.h_inst[i];
     I.A.chunk_ptr = M->chunk_ptr; I.A.row_len = M->row_len; I.A.col = M->col; I.A.val = M->val;
     I.A.D = M->D; I.A.C = M->C;
+    I.A32.chunk_ptr = M->chunk_ptr; I.A32.row_len = M->row_len; I.A32.col = M->col; I.A32.val = M->val32;
+    I.A32.D = M->D; I.A32.C = M->C;
     I.ns = ns[i];
     const int64_t D = M->D;
     const size_t nn = (size_t)ns[i] * ns[i];
@@ -558,6 +631,15 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
     I.P = p; p += GSLICES * nn;
     I.theta = p; p += ns[i];
     I.resid = p; p += ns[i];
+    I.V32 = nullptr;
+    I.W32 = nullptr;
+    if (f32) {  // after the FP64 part, 256-byte aligned
+      char* q = (char*)B.arena + off[i] +
+                (((sizeof(double) * (4 * D * ns[i] + 3 * nn + GSLICES * nn + 2 * ns[i] + RBLK * ns[i])) + 255) &
+                 ~(size_t)255);
+      I.V32 = (float*)q;
+      I.W32 = I.V32 + D * ns[i];
+    }
     I.rpart = p;
     for (int b = 0; b < ns[i] / nb; ++b) B.h_task.push_back({i, b});
   }
@@ -670,7 +752,16 @@ fd_status enqueue_iteration(fd_ctx* ctx, Batch& B) {
   FD_CUDA(ctx, cudaMemcpyAsync(B.d_par, B.h_par, sizeof(BParams) * B.n, cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaMemcpyAsync(B.d_mu, B.h_mu, sizeof(double) * B.mu_cap, cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaMemcpyAsync(B.d_kmax, B.h_kmax, sizeof(int), cudaMemcpyHostToDevice, st));
+  const dim3 cgrid((unsigned)std::max(1, ctx->num_sms * 2), B.n);
+  if (B.f32) {
+    k_bconvert<<<cgrid, 256, 0, st>>>(B.d_inst, B.d_par, 1);
+    FD_LAUNCHED(ctx);
+  }
   FD_TRY(launch_filter(ctx, B, 0));
+  if (B.f32) {
+    k_bconvert<<<cgrid, 256, 0, st>>>(B.d_inst, B.d_par, 0);
+    FD_LAUNCHED(ctx);
+  }
   FD_TRY(launch_ortho_rr(ctx, B));
   for (int i = 0; i < B.n; ++i) {
     const BInst& I = B.h_inst[i];
@@ -743,6 +834,9 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
   if (nb != 2 && nb != 4 && nb != 8 && nb != 16 && nb != 32 && nb != 64)
     return set_err(ctx, FD_ERR_ARG, "batched nb must be 2 .. 64");
   if (degree < 2 || !(tol > 0)) return set_err(ctx, FD_ERR_ARG, "need degree >= 2 and tol > 0");
+  if (opt.precision != FD_F64 && opt.precision != FD_F32) return set_err(ctx, FD_ERR_ARG, "bad precision");
+  const bool f32 = opt.precision == FD_F32;
+  if (f32 && nb < 4) return set_err(ctx, FD_ERR_ARG, "FP32 sweeps need nb >= 4");
   std::vector<int> ns(n_inst);
   for (int i = 0; i < n_inst; ++i) {
     if (!A[i] || !A[i]->identity)
@@ -770,7 +864,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
 
   Batch B;
   const size_t mu_cap = (size_t)n_inst * (n_max + 1);
-  fd_status s = batch_setup(ctx, B, n_inst, A, ns.data(), nb, warps, mu_cap);
+  fd_status s = batch_setup(ctx, B, n_inst, A, ns.data(), nb, warps, mu_cap, f32);
   if (s != FD_OK) { B.release(); return s; }
   s = set_kernel_smem(ctx, B.ns_max);
   if (s != FD_OK) { B.release(); return s; }
@@ -778,11 +872,16 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
   std::vector<double> lam_l(n_inst), lam_r(n_inst), widen(n_inst);
   std::vector<double> wl(n_inst), wr(n_inst);
   std::vector<int> deg(n_inst, degree), conv(n_inst, 0), iters(n_inst, 0);
-  std::vector<int64_t> nsp(n_inst, 0);
+  std::vector<int64_t> nsp(n_inst, 0), nsp32(n_inst, 0);
+  // the FP32 form's switch per instance (fd_solve's rule): FP32 sweeps until the
+  // largest wanted residual reaches 100 u32 |H| or fails to halve twice in a row
+  std::vector<int> use32(n_inst, f32 ? 1 : 0), stall(n_inst, 0);
+  std::vector<double> prev_max(n_inst, INFINITY), norm_h(n_inst, 0.0);
   for (int i = 0; i < n_inst; ++i) {
     s = spectral_bounds(ctx, A[i], lsteps, prob[i].seed, &lam_l[i], &lam_r[i]);
     if (s != FD_OK) { B.release(); return s; }
     widen[i] = 0.01 * (lam_r[i] - lam_l[i]);
+    norm_h[i] = std::max(std::fabs(lam_l[i]), std::fabs(lam_r[i]));
     k_bstart<<<(unsigned)cdiv(A[i]->D * ns[i], 256), 256, 0, st>>>(
         B.h_inst[i].V, A[i]->D * ns[i], fdrng::key(prob[i].seed, fdrng::STREAM_START));
     ctx->launches++;
@@ -790,7 +889,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
     wr[i] = prob[i].b;
   }
   // first iteration: no filter, orthonormalise + Rayleigh-Ritz
-  for (int i = 0; i < n_inst; ++i) B.h_par[i] = BParams{1, 0, 0, 0, 0.0, 0.0};
+  for (int i = 0; i < n_inst; ++i) B.h_par[i] = BParams{1, 0, 0, 0, 0.0, 0.0, 0, 0};
   *B.h_kmax = 0;
   // capture one iteration as a graph; replay it every outer iteration
   bool use_graph = true;
@@ -827,6 +926,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
       BParams& P = B.h_par[i];
       if (!P.active) continue;
       if (P.degree > 0) nsp[i] += P.degree;
+      if (P.degree > 0 && P.f32) nsp32[i] += P.degree;
       nsp[i] += 1;
       if (dev_par[i].flags & 2) {
         B.release();
@@ -840,7 +940,11 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
       const double tau = 0.5 * (prob[i].a + prob[i].b);
       std::vector<int> order = nearest(th, nsi, tau);
       int nconv = 0;
-      for (int q = 0; q < nt; ++q) nconv += rh[order[q]] <= tol;
+      double maxr = 0.0;
+      for (int q = 0; q < nt; ++q) {
+        nconv += rh[order[q]] <= tol;
+        maxr = std::max(maxr, rh[order[q]]);
+      }
       if (nconv == nt) {
         conv[i] = 1;
         P.active = 0;
@@ -866,10 +970,13 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
         s_r = std::max(s_r, t_r);
         auto ang = [&](double lam) { return std::acos(std::min(1.0, std::max(-1.0, alpha * lam + beta))); };
         const double dth = std::min(ang(s_l) - ang(t_l), ang(t_r) - ang(s_r));
-        long long nn = dth <= 0.0 ? n_max : (long long)std::ceil(c_n * M_PI / dth);
+        const double cn_i = prob[i].c_n > 0 ? prob[i].c_n : c_n;
+        const double ml_i = prob[i].m_l > 0 ? prob[i].m_l : m_l;
+        const double mr_i = prob[i].m_r > 0 ? prob[i].m_r : m_r;
+        long long nn = dth <= 0.0 ? n_max : (long long)std::ceil(cn_i * M_PI / dth);
         n = (int)std::max<long long>(degree, std::min<long long>(n_max, nn));
-        wl[i] = t_l - m_l * (t_l - s_l);
-        wr[i] = t_r + m_r * (s_r - t_r);
+        wl[i] = t_l - ml_i * (t_l - s_l);
+        wr[i] = t_r + mr_i * (s_r - t_r);
       }
       deg[i] = n;
       std::vector<double> mu = filter_coeffs(alpha * wl[i] + beta, alpha * wr[i] + beta, n);
@@ -879,6 +986,10 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
       P.alpha = alpha;
       P.beta = beta;
       P.flags = 0;
+      stall[i] = maxr > 0.5 * prev_max[i] ? stall[i] + 1 : 0;
+      if (use32[i] && (maxr <= 100.0 * 0x1.0p-24 * norm_h[i] || stall[i] >= 2)) use32[i] = 0;
+      prev_max[i] = maxr;
+      P.f32 = use32[i];
       mu_off += n + 1;
       kmax = std::max(kmax, n);
     }
@@ -897,6 +1008,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
     r.converged = conv[i];
     r.iterations = iters[i];
     r.n_spmmv = nsp[i];
+    r.n_spmmv_f32 = nsp32[i];
     r.final_degree = deg[i];
     r.ns = ns[i];
     r.lam_l = lam_l[i];
@@ -950,7 +1062,7 @@ fd_status fd_tune_batched(fd_ctx* ctx, int n_inst, const char* const* specs, int
           ctx->launches++;
           const double a = 2.0 / (M[i]->gersh_hi - M[i]->gersh_lo + 1e-3);
           const double b = -(M[i]->gersh_hi + M[i]->gersh_lo) / (M[i]->gersh_hi - M[i]->gersh_lo + 1e-3);
-          B.h_par[i] = BParams{1, probe_degree, 0, 0, a, b};
+          B.h_par[i] = BParams{1, probe_degree, 0, 0, a, b, 0, 0};
           const double vec = (double)nb * M[i]->D * 8.0, mat = (double)M[i]->nnz * 12.0;
           const int n = probe_degree;
           bytes += (ns / nb) * ((mat + 2 * vec) + (mat + 4 * vec) + (n - 3) * (mat + 5 * vec) + (mat + 4 * vec));

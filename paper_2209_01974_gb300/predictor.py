@@ -209,7 +209,10 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--out", default=WEIGHTS)
-    ap.add_argument("--log", default=os.path.join(HERE, "predictor_log.json"))
+    ap.add_argument("--log", default=os.path.join(HERE, "predictor_log.json"),
+                    help="the training run's metadata (read by the held-out test)")
+    ap.add_argument("--runs-log", default="predictor_runs.json",
+                    help="every labelling run and held-out solve (large; kept out of the package)")
     a = ap.parse_args(argv)
     ctx = fd_create(0)
     t0 = time.time()
@@ -237,12 +240,15 @@ def main(argv=None):
                                     "seconds": r0[2]["t_total"]},
                       "learned": {"n_spmmv": r1[2]["n_spmmv"], "converged": r1[2]["converged"],
                                   "seconds": r1[2]["t_total"], "params": r1[3]}})
+    h = sum(e["heuristic"]["n_spmmv"] for e in evals)
+    l = sum(e["learned"]["n_spmmv"] for e in evals)
     dump_log(a.log, {"problems": len(train_p), "holdout_problems": len(hold_p), "runs": len(runs),
                      "label_seconds": t_label, "nb": a.nb, "degree": a.degree, "tol": a.tol,
                      "grid": {"c_n": GRID_CN, "m": GRID_M}, "loss": hist,
-                     "labelled": int(ok.sum()), "holdout": evals, "runs_log": runs})
-    h = sum(e["heuristic"]["n_spmmv"] for e in evals)
-    l = sum(e["learned"]["n_spmmv"] for e in evals)
+                     "labelled": int(ok.sum()),
+                     "holdout_summary": {"problems": len(evals), "heuristic_spmmv": h, "learned_spmmv": l,
+                                         "learned_converged": sum(e["learned"]["converged"] for e in evals)}})
+    dump_log(a.runs_log, {"holdout": evals, "runs_log": runs})
     print(f"runs {len(runs)} in {t_label:.1f}s; held-out SpMMVs heuristic {h} learned {l} "
           f"({100 * (1 - l / max(1, h)):.1f}% fewer)")
 
