@@ -451,10 +451,13 @@ def run_gpu(args):
 
 
 TTS_SPEC = "anderson3d:L=48,W=16,seed=3"
-TTS_FORMS = {"f64": ("f64", False, "ritz"), "f64_lehmann": ("f64", False, "lehmann"),
-             "f32": ("f32", False, "ritz"), "f32_lehmann": ("f32", False, "lehmann"),
-             "f64_learned": ("f64", True, "ritz"), "f32_learned": ("f32", True, "ritz"),
-             "f32_learned_lehmann": ("f32", True, "lehmann")}
+# form: (precision, learned constants, intervals, finishing sweeps of the FP32 form)
+TTS_FORMS = {"f64": ("f64", False, "ritz", "f64"), "f64_lehmann": ("f64", False, "lehmann", "f64"),
+             "f32": ("f32", False, "ritz", "f64"), "f32_lehmann": ("f32", False, "lehmann", "f64"),
+             "f64_learned": ("f64", True, "ritz", "f64"), "f32_learned": ("f32", True, "ritz", "f64"),
+             "f32_learned_lehmann": ("f32", True, "lehmann", "f64"),
+             "ff": ("ff", False, "ritz", "f64"), "f32_ff": ("f32", False, "ritz", "ff"),
+             "f32_ff_learned": ("f32", True, "ritz", "ff")}
 
 
 def time_to_solution(ctx, forms, spec=TTS_SPEC, nt=32, nb=32, half_width=0.002, max_outer=40,
@@ -471,15 +474,17 @@ def time_to_solution(ctx, forms, spec=TTS_SPEC, nt=32, nb=32, half_width=0.002, 
                        f"nb={nb}, degree >= 100, tol 1e-9, max_outer {max_outer}, n_max {n_max}"}
     ref = None
     for name in forms:
-        prec, learned, iv = TTS_FORMS[name]
+        prec, learned, iv, finish = TTS_FORMS[name]
         th, rho, res, pred = predictor.solve_with(ctx, params if learned else None, A, -half_width, half_width,
                                                   nt, nb, 100, 1e-9, seed=0, precision=prec,
-                                                  max_outer=max_outer, n_max=n_max, intervals=iv)
+                                                  max_outer=max_outer, n_max=n_max, intervals=iv,
+                                                  finish=finish)
         th = np.sort(th)
         if ref is None and res["converged"]:
             ref = th
         out[name] = {"converged": res["converged"], "seconds": res["t_total"], "iterations": res["iterations"],
                      "n_spmmv": res["n_spmmv"], "n_spmmv_f32": res["n_spmmv_f32"],
+                     "n_spmmv_ff": res["n_spmmv_ff"],
                      "final_degree": res["final_degree"], "max_resid": float(rho.max()),
                      "max_abs_dtheta_vs_first_converged": (float(np.abs(th - ref).max())
                                                            if ref is not None and res["converged"] else None),
@@ -534,6 +539,7 @@ KERNEL_WORKLOADS = {
     "hubbard12": "hubbard:n_sites=12,n_up=6,n_dn=6,t=1,U=4,bc=periodic",
     "hubbard12kron": "hubbard:n_sites=12,n_up=6,n_dn=6,t=1,U=4,bc=periodic,kron=1",
     "roadgraph": "roadgraph:side=2000,q=0.3,seed=0",
+    "anderson48": TTS_SPEC,
 }
 
 
@@ -569,7 +575,7 @@ def run_ozaki_probe(D=524288, ns=NS):
 def run_kernel_only(prec, workload="stencil", nb=NB, degree=12, reps=5):
     """Profiling driver: one nb-wide block of a workload matrix (the L=128 stencil by
     default; the 14-site Hubbard ring, stored or matrix-free; the 4M-node road graph),
-    degree-`degree` filters in FP32 or FP64; used for the ncu captures summarised
+    degree-`degree` filters in FP32, FP64 or float-float; used for the ncu captures summarised
     under profiles/.  The matrix-free workloads read no matrix: their algorithmic
     bytes per step are the five vector passes alone."""
     import torch
@@ -583,6 +589,10 @@ def run_kernel_only(prec, workload="stencil", nb=NB, degree=12, reps=5):
     al, be = 2 / (hi - lo), -(hi + lo) / (hi - lo)
     mu = fd.fd_filter_coeffs(al * WINDOW[0] + be, al * WINDOW[1] + be, degree)
     V = torch.randn((D, nb), dtype=dt, device="cuda")
+    if prec == "ff":  # float-float pairs (D x nb x 2 float32) split from an FP64 block
+        Vff = torch.empty((D, nb, 2), dtype=torch.float32, device="cuda")
+        fd.fd_copy_block(ctx, V, Vff)
+        V = Vff
     W1, W2 = torch.empty_like(V), torch.empty_like(V)
     for _ in range(2):
         fd.fd_filter(ctx, A, V, mu, al, be, W1, W2)
@@ -594,7 +604,7 @@ def run_kernel_only(prec, workload="stencil", nb=NB, degree=12, reps=5):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps / degree
-    es = 8.0 if prec == "f64" else 4.0
+    es = 4.0 if prec == "f32" else 8.0
     mat_nnz = 0 if "kron=1" in KERNEL_WORKLOADS[workload] else nnz
     print(json.dumps({"kernel_only": prec, "workload": workload, "rows": D, "nnz": nnz, "nb": nb,
                       "degree": degree, "ms_per_step": ms,
@@ -639,24 +649,37 @@ def run_batched(args):
     t0 = time.perf_counter()
     out, res = fd.fd_solve_batched(ctx, mats, probs, nb, 200, 1e-9, raise_noconv=False,
                                    cta_warps=tune["cta_warps"], max_outer=args.max_outer,
-                                   n_max=args.n_max, precision=args.precision)
+                                   n_max=args.n_max, precision=args.precision, finish=args.finish,
+                                   verbose=int(args.verbose))
     t_batched = time.perf_counter() - t0
+    rows = sum(m.D for m in mats)
+    head = {"phase": "batched", "precision": args.precision, "finish": args.finish,
+            "learned": bool(args.learned),
+            "max_outer": args.max_outer, "n_max": args.n_max, "rows_total": rows, "tuner": tune,
+            "tuner_seconds": t_tune, "batched_seconds": t_batched,
+            "converged_batched": sum(r["converged"] for r in res),
+            "n_spmmv_batched": int(sum(r["n_spmmv"] for r in res)),
+            "n_spmmv_f32_batched": int(sum(r["n_spmmv_f32"] for r in res)),
+            "n_spmmv_ff_batched": int(sum(r["n_spmmv_ff"] for r in res)),
+            "used_graph": res[0]["used_graph"]}
+    print(json.dumps(head), flush=True)
+    if args.no_sequential:
+        return 0
     t0 = time.perf_counter()
     seq, seq_th = [], []
     for m, (a, b, nt, sd, cn, ml, mr) in zip(mats, probs):
         extra = {"c_n": cn, "m_l": ml, "m_r": mr} if params is not None else {}
         th, rho, r = fd.fd_solve(ctx, m, a, b, nt, nb, 200, 1e-9, seed=sd, raise_noconv=False,
                                  max_outer=args.max_outer, n_max=args.n_max, precision=args.precision,
-                                 **extra)
+                                 finish=args.finish, **extra)
         seq.append(r)
         seq_th.append(th)
     t_seq = time.perf_counter() - t0
     both = [i for i in range(n) if res[i]["converged"] and seq[i]["converged"]]
     dth = max((float(np.abs(out[i][0] - seq_th[i]).max()) for i in both), default=None)
-    rows = sum(m.D for m in mats)
     line = {"workload": f"batched: {n} Anderson instances L 16..48, W 2..16, 16 pairs at E=0 (window "
                         "+-0.01), nb from tuner, degree >= 200, tol 1e-9",
-            "precision": args.precision, "learned": bool(args.learned),
+            "precision": args.precision, "finish": args.finish, "learned": bool(args.learned),
             "max_outer": args.max_outer, "n_max": args.n_max,
             "rows_total": rows, "tuner": tune, "tuner_seconds": t_tune,
             "batched_seconds": t_batched, "sequential_seconds": t_seq,
@@ -665,6 +688,7 @@ def run_batched(args):
             "converged_sequential": sum(r["converged"] for r in seq),
             "n_spmmv_batched": int(sum(r["n_spmmv"] for r in res)),
             "n_spmmv_f32_batched": int(sum(r["n_spmmv_f32"] for r in res)),
+            "n_spmmv_ff_batched": int(sum(r["n_spmmv_ff"] for r in res)),
             "used_graph": res[0]["used_graph"],
             "max_abs_dtheta_batched_vs_sequential": dth,
             "max_resid_batched": float(max((o[1][np.isfinite(o[1])].max() for o in out
@@ -759,7 +783,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--kernel-only", choices=["f32", "f64", "cholqr2"], default=None,
+    ap.add_argument("--kernel-only", choices=["f32", "f64", "ff", "cholqr2"], default=None,
                     help="profiling driver: degree-12 filters on one nb-wide block")
     ap.add_argument("--workload", choices=sorted(KERNEL_WORKLOADS), default="stencil")
     ap.add_argument("--nb", type=int, default=NB)
@@ -767,9 +791,14 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="batched-instances measurement (64 Anderson problems) instead of the bench")
     ap.add_argument("--instances", type=int, default=64)
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "ff"],
                     help="precision form of --batched")
+    ap.add_argument("--finish", default="f64", choices=["f64", "ff"],
+                    help="--batched: finishing sweeps of the FP32 form (FP64 or float-float)")
     ap.add_argument("--learned", action="store_true", help="--batched: each instance's learned constants")
+    ap.add_argument("--verbose", action="store_true", help="--batched / --tts: per-iteration log on stderr")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="--batched: time the batched solve only, not the one-by-one solves")
     ap.add_argument("--max-outer", type=int, default=40)
     ap.add_argument("--n-max", type=int, default=100000)
     ap.add_argument("--learned-eval", action="store_true",

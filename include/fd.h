@@ -56,7 +56,13 @@ typedef enum {
   FD_ERR_BOUNDS = 7     /* a device-side bounds check fired (bad CSR / index) */
 } fd_status;
 
-typedef enum { FD_F64 = 0, FD_F32 = 1 } fd_prec;
+/* Arithmetic of the filter sweeps.  FD_FF ("float-float"): every value is an
+ * unevaluated sum hi + lo of two floats, stored as the pair (hi, lo) in 8
+ * bytes, with sums and products from error-free transformations in FP32
+ * arithmetic (about 2^-48 relative, FP32 exponent range).  Not in the paper:
+ * GB300 runs FP64 at about 1/64 of its FP32 rate, so FP64-accurate sweeps are
+ * cheaper in FP32 pairs than in FP64. */
+typedef enum { FD_F64 = 0, FD_F32 = 1, FD_FF = 2 } fd_prec;
 
 /* ------------------------------------------------------------------ context */
 
@@ -165,8 +171,11 @@ fd_status fd_spectral_bounds(fd_ctx* ctx, const fd_matrix* A, int steps,
  * V <- V + mu_k W2 (Alg. 2 fuses the SpMV with the vector update so that W2 is
  * not read twice).
  *   prec    FD_F64: V, W1, W2 are double and H's FP64 values are used;
- *           FD_F32: V, W1, W2 are float, H's FP32 copy, FP32 accumulation.
- *   nb      2, 4, 8, 16, 32, 64 or 128 (FP64); 4 .. 128 (FP32)
+ *           FD_F32: V, W1, W2 are float, H's FP32 copy, FP32 accumulation;
+ *           FD_FF: V, W1, W2 hold float-float pairs (2 floats per element,
+ *           ld counted in elements), H's float-float copy of its FP64 values;
+ *           stored matrices only (kron = 0 gives FD_ERR_ARG).
+ *   nb      2, 4, 8, 16, 32, 64 or 128 (FP64, FF); 4 .. 128 (FP32)
  *   degree  n >= 2 (Alg. 2 takes degree n >= 2); mu: HOST array of n+1 doubles
  *   W1, W2  device workspaces, D x nb each with leading dimension ldw
  *           (contents are overwritten)
@@ -243,7 +252,9 @@ fd_status fd_rotate(fd_ctx* ctx, double* V, int64_t ldv, int64_t D, int n, const
 /* Copy the D x n device block src (leading dimension lds, type sp) into dst
  * (ldd, type dp), rounding FP64 to FP32 or widening FP32 to FP64 as needed
  * (the FP32 filter form moves bundles between the FP64 search block and FP32
- * sweep buffers with this call). */
+ * sweep buffers with this call).  FP64 -> FD_FF splits each value into its
+ * nearest float and the nearest float to the remainder; FD_FF -> FP64 adds
+ * the pair (exact).  FD_F32 <-> FD_FF is FD_ERR_ARG. */
 fd_status fd_copy_block(fd_ctx* ctx, const void* src, fd_prec sp, int64_t lds, void* dst,
                         fd_prec dp, int64_t ldd, int64_t D, int n);
 
@@ -299,8 +310,9 @@ typedef struct {
   uint64_t seed;     /* start block: SplitMix64 stream 2 (Lanczos: stream 3) [0] */
   int precision;     /* FD_F64: all-FP64 sweeps; FD_F32: FP32 sweeps until the
                         largest wanted residual reaches 100 u32 |H| or fails to
-                        halve in two iterations in a row, then FP64 sweeps
-                        [FD_F64] */
+                        halve in two iterations in a row, then the finishing
+                        sweeps of `finish`; FD_FF: all sweeps in float-float
+                        (stored matrices only) [FD_F64] */
   double c_n;        /* degree = c_n pi / dtheta [4] */
   double m_l, m_r;   /* window edge = target edge + m (search edge - target edge) [0.5] */
   int verbose;       /* 1: print one line per outer iteration to stderr */
@@ -319,7 +331,13 @@ typedef struct {
                         misses part of the spectrum is widened by 2 % of its
                         width on a side whenever a Ritz value falls outside it
                         on that side [0, 0] */
+  int finish;        /* finishing sweeps of the FD_F32 form: FD_FINISH_F64
+                        (FP64, the paper's FP64 sweeps) or FD_FINISH_FF
+                        (float-float, FP64-like accuracy at FP32 arithmetic
+                        rates; stored matrices only) [FD_FINISH_F64] */
 } fd_options;
+
+enum { FD_FINISH_F64 = 0, FD_FINISH_FF = 1 };
 
 enum { FD_INTERVALS_RITZ = 0, FD_INTERVALS_LEHMANN = 1 };
 
@@ -335,6 +353,7 @@ typedef struct {
   double t_total, t_bounds, t_filter, t_ortho, t_rr; /* seconds (CUDA events) */
   double filter_bytes; /* algorithmic bytes of all filter steps (kappa = 5) */
   int used_graph;      /* fd_solve_batched: 1 if the iterations ran as a CUDA graph */
+  int64_t n_spmmv_ff;  /* SpMMVs in float-float sweeps */
 } fd_result;
 
 /* Lehmann bounds (Lehmann 1963; Sec. 2 takes the FD target and search
@@ -388,6 +407,7 @@ typedef struct {
   int64_t D;            /* consistency checks on resume */
   int ns;
   uint64_t seed;
+  int64_t n_spmmv_ff;
 } fd_checkpoint;
 
 /* fd_solve in slices: starting from *ck (iteration 0: a fresh solve; else the

@@ -23,7 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 FD_OK, FD_ERR_ARG, FD_ERR_CUDA, FD_ERR_OOM, FD_ERR_NOCONV, FD_ERR_BREAKDOWN, FD_ERR_TIMEOUT, \
     FD_ERR_BOUNDS = range(8)
-FD_F64, FD_F32 = 0, 1
+FD_F64, FD_F32, FD_FF = 0, 1, 2
 STATUS_NAMES = {0: "FD_OK", 1: "FD_ERR_ARG", 2: "FD_ERR_CUDA", 3: "FD_ERR_OOM", 4: "FD_ERR_NOCONV",
                 5: "FD_ERR_BREAKDOWN", 6: "FD_ERR_TIMEOUT", 7: "FD_ERR_BOUNDS"}
 
@@ -43,9 +43,10 @@ class fd_options(ctypes.Structure):
     _fields_ = [("ns", _i32), ("max_outer", _i32), ("n_max", _i32), ("lanczos_steps", _i32),
                 ("seed", ctypes.c_uint64), ("precision", _i32), ("c_n", _dbl), ("m_l", _dbl),
                 ("m_r", _dbl), ("verbose", _i32), ("cta_warps", _i32), ("intervals", _i32),
-                ("lam_l", _dbl), ("lam_r", _dbl)]
+                ("lam_l", _dbl), ("lam_r", _dbl), ("finish", _i32)]
 
 FD_INTERVALS_RITZ, FD_INTERVALS_LEHMANN = 0, 1
+FD_FINISH_F64, FD_FINISH_FF = 0, 1
 
 
 class fd_checkpoint(ctypes.Structure):
@@ -53,7 +54,7 @@ class fd_checkpoint(ctypes.Structure):
                 ("stall", _i32), ("lam_l", _dbl), ("lam_r", _dbl), ("widen", _dbl), ("norm_h", _dbl),
                 ("window_l", _dbl), ("window_r", _dbl), ("prev_max", _dbl), ("n_spmmv", _i64),
                 ("n_spmmv_f32", _i64), ("filter_bytes", _dbl), ("D", _i64), ("ns", _i32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("n_spmmv_ff", _i64)]
 
 
 class fd_problem(ctypes.Structure):
@@ -66,7 +67,7 @@ class fd_result(ctypes.Structure):
                 ("n_spmmv_f32", _i64), ("final_degree", _i32), ("ns", _i32), ("lam_l", _dbl),
                 ("lam_r", _dbl), ("window_l", _dbl), ("window_r", _dbl), ("t_total", _dbl),
                 ("t_bounds", _dbl), ("t_filter", _dbl), ("t_ortho", _dbl), ("t_rr", _dbl),
-                ("filter_bytes", _dbl), ("used_graph", _i32)]
+                ("filter_bytes", _dbl), ("used_graph", _i32), ("n_spmmv_ff", _i64)]
 
 
 _SIGS = {
@@ -149,8 +150,15 @@ def _dptr(a, dtype):
 
 
 def _block(t, name):
-    """(pointer, ld, D, ncols, prec) of a row-major CUDA tensor block."""
+    """(pointer, ld, D, ncols, prec) of a row-major CUDA tensor block: a 2-D
+    float64 or float32 tensor, or a D x n x 2 float32 tensor holding
+    float-float values (hi, lo) (FD_FF; ld counted in elements)."""
     import torch
+    if (isinstance(t, torch.Tensor) and t.is_cuda and t.dim() == 3 and t.shape[2] == 2
+            and t.dtype == torch.float32):
+        if t.stride(2) != 1 or t.stride(1) != 2 or t.stride(0) % 2:
+            raise ValueError(f"{name}: float-float blocks need (hi, lo) pairs in row-major rows")
+        return t.data_ptr(), t.stride(0) // 2, t.shape[0], t.shape[1], FD_FF
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dim() != 2:
         raise ValueError(f"{name} must be a 2-D CUDA tensor")
     if t.stride(1) != 1:
@@ -365,7 +373,8 @@ def fd_rotate(ctx, V, M, upper=False):
 
 
 def fd_copy_block(ctx, src, dst):
-    """dst <- src (same shape), converting between float64 and float32."""
+    """dst <- src (same shape), converting between float64 and float32 or
+    float-float (D x n x 2 float32) blocks."""
     ps, lds, D, n, sp = _block(src, "src")
     pd, ldd, D2, n2, dp = _block(dst, "dst")
     if (D, n) != (D2, n2):
@@ -416,7 +425,10 @@ def _options(opts):
     o = fd_options()
     for k, v in opts.items():
         if k == "precision" and isinstance(v, str):
-            v = FD_F32 if v in ("f32", "fp32", "float32") else FD_F64
+            v = {"f64": FD_F64, "fp64": FD_F64, "float64": FD_F64, "f32": FD_F32, "fp32": FD_F32,
+                 "float32": FD_F32, "ff": FD_FF}[v]
+        if k == "finish" and isinstance(v, str):
+            v = {"f64": FD_FINISH_F64, "ff": FD_FINISH_FF}[v]
         if k == "intervals" and isinstance(v, str):
             v = {"ritz": FD_INTERVALS_RITZ, "lehmann": FD_INTERVALS_LEHMANN}[v]
         setattr(o, k, v)

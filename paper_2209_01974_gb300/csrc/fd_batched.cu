@@ -21,6 +21,7 @@
 
 #include "fd_internal.cuh"
 #include "fd_step.cuh"
+#include "fd_ff.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -28,12 +29,14 @@ namespace fdi {
 namespace {
 
 using namespace step;
+using ffa::ff;
 
 constexpr int BMAX_NS = 96;  // single-CTA shared-memory Jacobi / Cholesky limit
 
 struct BInst {
   SellArgs<double> A;
   SellArgs<float> A32;  // the same SELL arrays with the FP32 values
+  SellArgs<ff> Aff;     // ... and with the float-float values
   double* V;      // D x ns, ld = ns
   float* V32;     // FP32 copy of V for FP32 sweeps (nullptr unless the FP32 form is on)
   float* W32;     // (ns / nb) bundles x 2 x D x nb
@@ -57,7 +60,7 @@ struct BParams {  // rewritten by the host before every outer iteration
   int flags;      // device-written: 1 = a Cholesky pass was shifted, 2 = breakdown
   double alpha, beta;
   int f32;        // 1: this iteration's filter runs in FP32 (V32, W32, FP32 values)
-  int pad;
+  int ff;         // 1: it runs in float-float (V and W hold (hi, lo) pairs in place)
 };
 
 struct BTask {
@@ -160,7 +163,47 @@ __device__ __forceinline__ void batched_row_group_f32(const BatchArgs& b, int t,
   }
 }
 
+// float-float sweeps of an instance (its FP32 form's finish, or the FF form):
+// the same steps on V and W reinterpreted as (hi, lo) pairs, which k_bconvert
+// writes in place of the doubles before the filter and turns back after it
 template <int NB>
+__device__ __forceinline__ void batched_row_group_ff(const BatchArgs& b, int t, int64_t lrow0, int k) {
+  const BTask tk = b.task[t];
+  const BInst& I = b.inst[tk.inst];
+  const BParams& P = b.par[tk.inst];
+  const int64_t D = I.A.D;
+  const int n = P.degree;
+  if (!P.active || k > n) return;
+  ff* V = reinterpret_cast<ff*>(I.V + (int64_t)tk.bundle * NB);
+  ff* W1 = reinterpret_cast<ff*>(I.W + (int64_t)tk.bundle * 2 * D * NB);
+  ff* W2 = W1 + D * NB;
+  const double* mu = b.mu + P.mu_off;
+  StepArgs<ff> s{};
+  if (k == 1) {
+    s.X = V; s.ldx = I.ns; s.Y = W1; s.ldy = NB;
+    s.c_ax = ff(P.alpha); s.c_x = ff(P.beta);
+    cheb_rows<ff, NB, MODE_SPMMV>(I.Aff, s, lrow0);
+  } else if (k == 2) {
+    s.X = W1; s.ldx = NB; s.Z = V; s.ldz = I.ns;
+    s.Y = n > 2 ? W2 : nullptr; s.ldy = NB;
+    s.Vout = V; s.ldvo = I.ns;
+    s.c_ax = ff(2 * P.alpha); s.c_x = ff(2 * P.beta);
+    s.mu0 = ff(mu[0]); s.mu1 = ff(mu[1]); s.mu2 = ff(mu[2]);
+    cheb_rows<ff, NB, MODE_SECOND>(I.Aff, s, lrow0);
+  } else {
+    ff* X = (k & 1) ? W2 : W1;
+    ff* Z = (k & 1) ? W1 : W2;
+    s.X = X; s.ldx = NB; s.Z = Z; s.ldz = NB;
+    s.Y = k < n ? Z : nullptr; s.ldy = NB;
+    s.Vin = V; s.ldvi = I.ns; s.Vout = V; s.ldvo = I.ns;
+    s.c_ax = ff(2 * P.alpha); s.c_x = ff(2 * P.beta); s.mu2 = ff(mu[k]);
+    cheb_rows<ff, NB, MODE_GENERIC>(I.Aff, s, lrow0);
+  }
+}
+
+// FF: the instantiation with the float-float path, launched only by solves
+// that can use it (its extra registers then cost nothing elsewhere)
+template <int NB, bool FF>
 __global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
   using L = Layout<double, NB>;
   extern __shared__ int64_t s_off[];  // n_tasks + 1
@@ -193,6 +236,12 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
           continue;
         }
       }
+      if constexpr (FF) {
+        if (!b.spmmv_only && b.par[inst].ff) {
+          batched_row_group_ff<NB>(b, lo, lrow0, k);
+          continue;
+        }
+      }
       batched_row_group<NB>(b, lo, lrow0, k);
     }
     if (!b.spmmv_only) grid.sync();
@@ -201,12 +250,30 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
 
 // V32 <- (float) V before an FP32 filter, V <- (double) V32 after it, for the
 // instances whose filter runs in FP32 this iteration (blockIdx.y = instance)
+// For float-float filters the same kernel splits each double of V in place
+// into its (hi, lo) pair and adds the pair back afterwards.
 __global__ void k_bconvert(const BInst* insts, const BParams* par, int to32) {
   const BInst& I = insts[blockIdx.y];
   const BParams& P = par[blockIdx.y];
-  if (!P.active || !P.f32 || P.degree == 0 || !I.V32) return;
+  if (!P.active || P.degree == 0) return;
   const int64_t n = I.A.D * I.ns;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, de = (int64_t)gridDim.x * blockDim.x;
+  if (P.ff) {
+    float2* F = reinterpret_cast<float2*>(I.V);
+    for (int64_t e = e0; e < n; e += de) {
+      if (to32) {
+        const double v = I.V[e];
+        const float hi = __double2float_rn(v);
+        F[e] = make_float2(hi, __double2float_rn(v - (double)hi));
+      } else {
+        const float2 f = F[e];
+        I.V[e] = (double)f.x + (double)f.y;
+      }
+    }
+    return;
+  }
+  if (!P.f32 || !I.V32) return;
+  for (int64_t e = e0; e < n; e += de) {
     if (to32) I.V32[e] = (float)I.V[e];
     else I.V[e] = (double)I.V32[e];
   }
@@ -540,6 +607,7 @@ __global__ void k_bstart(double* V, int64_t n, uint64_t key) {
 struct Batch {
   int n = 0, nb = 0, warps = WARPS, ns_max = 0;
   bool f32 = false;  // FP32 sweeps available (the FP32 form)
+  bool ff = false;   // float-float sweeps possible (FF form or float-float finish)
   std::vector<BInst> h_inst;
   std::vector<BTask> h_task;
   std::vector<int64_t> h_off;
@@ -572,26 +640,29 @@ struct Batch {
 };
 
 template <int NB>
-const void* filter_kernel() { return (const void*)k_batched_filter<NB>; }
+const void* filter_kernel(bool with_ff) {
+  return with_ff ? (const void*)k_batched_filter<NB, true> : (const void*)k_batched_filter<NB, false>;
+}
 
-const void* filter_kernel_for(int nb) {
+const void* filter_kernel_for(int nb, bool with_ff) {
   switch (nb) {
-    case 2: return filter_kernel<2>();
-    case 4: return filter_kernel<4>();
-    case 8: return filter_kernel<8>();
-    case 16: return filter_kernel<16>();
-    case 32: return filter_kernel<32>();
-    case 64: return filter_kernel<64>();
+    case 2: return filter_kernel<2>(with_ff);
+    case 4: return filter_kernel<4>(with_ff);
+    case 8: return filter_kernel<8>(with_ff);
+    case 16: return filter_kernel<16>(with_ff);
+    case 32: return filter_kernel<32>(with_ff);
+    case 64: return filter_kernel<64>(with_ff);
     default: return nullptr;
   }
 }
 
 fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, const int* ns,
-                      int nb, int warps, size_t mu_cap, bool f32 = false) {
+                      int nb, int warps, size_t mu_cap, bool f32 = false, bool with_ff = false) {
   B.n = n;
   B.nb = nb;
   B.warps = warps;
   B.f32 = f32;
+  B.ff = with_ff;
   // rows per warp of the FP64 step; the FP32 step covers twice as many
   const int rpw = (32 / std::min(32, nb * 8 / 16)) * (f32 ? 2 : 1);
   // arena layout per instance
@@ -618,6 +689,8 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
     I.A.D = M->D; I.A.C = M->C;
     I.A32.chunk_ptr = M->chunk_ptr; I.A32.row_len = M->row_len; I.A32.col = M->col; I.A32.val = M->val32;
     I.A32.D = M->D; I.A32.C = M->C;
+    I.Aff.chunk_ptr = M->chunk_ptr; I.Aff.row_len = M->row_len; I.Aff.col = M->col;
+    I.Aff.val = reinterpret_cast<const ff*>(M->valff); I.Aff.D = M->D; I.Aff.C = M->C;
     I.ns = ns[i];
     const int64_t D = M->D;
     const size_t nn = (size_t)ns[i] * ns[i];
@@ -668,7 +741,7 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
   FD_CUDA(ctx, cudaMallocHost(&B.h_kmax, sizeof(int)));
   FD_CUDA(ctx, cudaMallocHost(&B.h_out, sizeof(double) * 2 * n * B.ns_max + sizeof(BParams) * n));
   // persistent filter grid: every CTA resident
-  const void* kf = filter_kernel_for(nb);
+  const void* kf = filter_kernel_for(nb, B.ff);
   if (!kf) return set_err(ctx, FD_ERR_ARG, "batched filter supports nb = 2 .. 64");
   B.smem_filter = sizeof(int64_t) * (B.h_task.size() + 1);
   if (B.smem_filter > 48 * 1024)
@@ -685,7 +758,7 @@ fd_status launch_filter(fd_ctx* ctx, Batch& B, int spmmv_only) {
   a.inst = B.d_inst; a.par = B.d_par; a.task = B.d_task; a.task_off = B.d_off; a.mu = B.d_mu;
   a.kmax = B.d_kmax; a.n_tasks = (int)B.h_task.size(); a.nb = B.nb; a.spmmv_only = spmmv_only;
   void* args[] = {&a};
-  const void* kf = filter_kernel_for(B.nb);
+  const void* kf = filter_kernel_for(B.nb, B.ff);
   if (spmmv_only) {
     FD_CUDA(ctx, cudaLaunchKernel(kf, B.grid, B.warps * 32, args, B.smem_filter, ctx->stream));
   } else {
@@ -753,12 +826,12 @@ fd_status enqueue_iteration(fd_ctx* ctx, Batch& B) {
   FD_CUDA(ctx, cudaMemcpyAsync(B.d_mu, B.h_mu, sizeof(double) * B.mu_cap, cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaMemcpyAsync(B.d_kmax, B.h_kmax, sizeof(int), cudaMemcpyHostToDevice, st));
   const dim3 cgrid((unsigned)std::max(1, ctx->num_sms * 2), B.n);
-  if (B.f32) {
+  if (B.f32 || B.ff) {
     k_bconvert<<<cgrid, 256, 0, st>>>(B.d_inst, B.d_par, 1);
     FD_LAUNCHED(ctx);
   }
   FD_TRY(launch_filter(ctx, B, 0));
-  if (B.f32) {
+  if (B.f32 || B.ff) {
     k_bconvert<<<cgrid, 256, 0, st>>>(B.d_inst, B.d_par, 0);
     FD_LAUNCHED(ctx);
   }
@@ -834,8 +907,13 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
   if (nb != 2 && nb != 4 && nb != 8 && nb != 16 && nb != 32 && nb != 64)
     return set_err(ctx, FD_ERR_ARG, "batched nb must be 2 .. 64");
   if (degree < 2 || !(tol > 0)) return set_err(ctx, FD_ERR_ARG, "need degree >= 2 and tol > 0");
-  if (opt.precision != FD_F64 && opt.precision != FD_F32) return set_err(ctx, FD_ERR_ARG, "bad precision");
+  if (opt.precision != FD_F64 && opt.precision != FD_F32 && opt.precision != FD_FF)
+    return set_err(ctx, FD_ERR_ARG, "bad precision");
+  if (opt.finish != FD_FINISH_F64 && opt.finish != FD_FINISH_FF)
+    return set_err(ctx, FD_ERR_ARG, "finish must be FD_FINISH_F64 or FD_FINISH_FF");
   const bool f32 = opt.precision == FD_F32;
+  // float-float sweeps: the FF form, or the FP32 form's finish
+  const bool ffs = opt.precision == FD_FF || (f32 && opt.finish == FD_FINISH_FF);
   if (f32 && nb < 4) return set_err(ctx, FD_ERR_ARG, "FP32 sweeps need nb >= 4");
   std::vector<int> ns(n_inst);
   for (int i = 0; i < n_inst; ++i) {
@@ -864,7 +942,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
 
   Batch B;
   const size_t mu_cap = (size_t)n_inst * (n_max + 1);
-  fd_status s = batch_setup(ctx, B, n_inst, A, ns.data(), nb, warps, mu_cap, f32);
+  fd_status s = batch_setup(ctx, B, n_inst, A, ns.data(), nb, warps, mu_cap, f32, ffs);
   if (s != FD_OK) { B.release(); return s; }
   s = set_kernel_smem(ctx, B.ns_max);
   if (s != FD_OK) { B.release(); return s; }
@@ -872,7 +950,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
   std::vector<double> lam_l(n_inst), lam_r(n_inst), widen(n_inst);
   std::vector<double> wl(n_inst), wr(n_inst);
   std::vector<int> deg(n_inst, degree), conv(n_inst, 0), iters(n_inst, 0);
-  std::vector<int64_t> nsp(n_inst, 0), nsp32(n_inst, 0);
+  std::vector<int64_t> nsp(n_inst, 0), nsp32(n_inst, 0), nspff(n_inst, 0);
   // the FP32 form's switch per instance (fd_solve's rule): FP32 sweeps until the
   // largest wanted residual reaches 100 u32 |H| or fails to halve twice in a row
   std::vector<int> use32(n_inst, f32 ? 1 : 0), stall(n_inst, 0);
@@ -919,6 +997,16 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
       if (s != FD_OK) { B.release(); return s; }
     }
     FD_CUDA(ctx, cudaStreamSynchronize(st));
+    if (opt.verbose) {
+      int n32 = 0;
+      for (int i = 0; i < n_inst; ++i) n32 += B.h_par[i].active && B.h_par[i].f32 && B.h_par[i].degree > 0;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float msv = 0;
+      cudaEventElapsedTime(&msv, e0, e1);
+      fprintf(stderr, "batched it %d: active %d (FP32 sweeps %d), top degree %d, elapsed %.2f s\n", it,
+              n_left, n32, *B.h_kmax, msv * 1e-3);
+    }
     const BParams* dev_par = (const BParams*)(B.h_out + (size_t)2 * n_inst * B.ns_max);
     int kmax = 0;
     size_t mu_off = 0;
@@ -927,6 +1015,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
       if (!P.active) continue;
       if (P.degree > 0) nsp[i] += P.degree;
       if (P.degree > 0 && P.f32) nsp32[i] += P.degree;
+      if (P.degree > 0 && P.ff) nspff[i] += P.degree;
       nsp[i] += 1;
       if (dev_par[i].flags & 2) {
         B.release();
@@ -990,6 +1079,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
       if (use32[i] && (maxr <= 100.0 * 0x1.0p-24 * norm_h[i] || stall[i] >= 2)) use32[i] = 0;
       prev_max[i] = maxr;
       P.f32 = use32[i];
+      P.ff = !use32[i] && ffs;
       mu_off += n + 1;
       kmax = std::max(kmax, n);
     }
@@ -1009,6 +1099,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
     r.iterations = iters[i];
     r.n_spmmv = nsp[i];
     r.n_spmmv_f32 = nsp32[i];
+    r.n_spmmv_ff = nspff[i];
     r.final_degree = deg[i];
     r.ns = ns[i];
     r.lam_l = lam_l[i];

@@ -433,6 +433,25 @@ __global__ void k_f32_to_f64(const float* s, int64_t lds, double* d, int64_t ldd
   int j = (int)(t % n);
   d[i * ldd + j] = (double)s[i * lds + j];
 }
+// FP64 <-> float-float (element = 2 floats): hi the nearest float, lo the
+// nearest float to the exact FP64 remainder; back, hi + lo is exact in FP64
+__global__ void k_f64_to_ff(const double* s, int64_t lds, float* d, int64_t ldd, int64_t D, int n) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= D * n) return;
+  int64_t i = t / n;
+  int j = (int)(t % n);
+  const double v = s[i * lds + j];
+  const float hi = __double2float_rn(v);
+  *reinterpret_cast<float2*>(d + 2 * (i * ldd + j)) = make_float2(hi, __double2float_rn(v - (double)hi));
+}
+__global__ void k_ff_to_f64(const float* s, int64_t lds, double* d, int64_t ldd, int64_t D, int n) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= D * n) return;
+  int64_t i = t / n;
+  int j = (int)(t % n);
+  const float2 v = *reinterpret_cast<const float2*>(s + 2 * (i * lds + j));
+  d[i * ldd + j] = (double)v.x + (double)v.y;
+}
 
 }  // namespace
 
@@ -695,6 +714,18 @@ fd_status copy_cols_f32_to_f64(fd_ctx* ctx, const float* src, int64_t lds, doubl
   FD_LAUNCHED(ctx);
   return FD_OK;
 }
+fd_status copy_cols_f64_to_ff(fd_ctx* ctx, const double* src, int64_t lds, float* dst, int64_t ldd,
+                              int64_t D, int n) {
+  k_f64_to_ff<<<(unsigned)cdiv(D * n, 256), 256, 0, ctx->stream>>>(src, lds, dst, ldd, D, n);
+  FD_LAUNCHED(ctx);
+  return FD_OK;
+}
+fd_status copy_cols_ff_to_f64(fd_ctx* ctx, const float* src, int64_t lds, double* dst, int64_t ldd,
+                              int64_t D, int n) {
+  k_ff_to_f64<<<(unsigned)cdiv(D * n, 256), 256, 0, ctx->stream>>>(src, lds, dst, ldd, D, n);
+  FD_LAUNCHED(ctx);
+  return FD_OK;
+}
 
 }  // namespace fdi
 
@@ -743,16 +774,21 @@ fd_status fd_copy_block(fd_ctx* ctx, const void* src, fd_prec sp, int64_t lds, v
                         int64_t ldd, int64_t D, int n) {
   if (!ctx) return FD_ERR_ARG;
   ctx->err.clear();
-  if (!src || !dst || D < 0 || n < 0 || lds < n || ldd < n || (sp != FD_F64 && sp != FD_F32) ||
-      (dp != FD_F64 && dp != FD_F32))
-    return set_err(ctx, FD_ERR_ARG, "need buffers, D, n >= 0, lds, ldd >= n and FD_F64/FD_F32");
+  auto known = [](fd_prec p) { return p == FD_F64 || p == FD_F32 || p == FD_FF; };
+  if (!src || !dst || D < 0 || n < 0 || lds < n || ldd < n || !known(sp) || !known(dp) ||
+      (sp == FD_F32 && dp == FD_FF) || (sp == FD_FF && dp == FD_F32))
+    return set_err(ctx, FD_ERR_ARG, "need buffers, D, n >= 0, lds, ldd >= n and a supported type pair");
   if (D == 0 || n == 0) return FD_OK;
   FD_CUDA(ctx, cudaSetDevice(ctx->device));
   if (sp == FD_F64 && dp == FD_F32)
     return copy_cols_f64_to_f32(ctx, (const double*)src, lds, (float*)dst, ldd, D, n);
   if (sp == FD_F32 && dp == FD_F64)
     return copy_cols_f32_to_f64(ctx, (const float*)src, lds, (double*)dst, ldd, D, n);
-  const size_t es = sp == FD_F64 ? 8 : 4;
+  if (sp == FD_F64 && dp == FD_FF)
+    return copy_cols_f64_to_ff(ctx, (const double*)src, lds, (float*)dst, ldd, D, n);
+  if (sp == FD_FF && dp == FD_F64)
+    return copy_cols_ff_to_f64(ctx, (const float*)src, lds, (double*)dst, ldd, D, n);
+  const size_t es = sp == FD_F32 ? 4 : 8;
   FD_CUDA(ctx, cudaMemcpy2DAsync(dst, ldd * es, src, lds * es, n * es, D, cudaMemcpyDeviceToDevice,
                                  ctx->stream));
   return FD_OK;

@@ -16,15 +16,18 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "fd_internal.cuh"
 #include "fd_step.cuh"
+#include "fd_ff.cuh"
 
 namespace fdi {
 namespace {
 
 using namespace step;
+using ffa::ff;
 
 template <typename T, int NB, int MODE>
 __global__ void __launch_bounds__(step_warps<T>() * 32, sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64)
@@ -111,11 +114,17 @@ fd_status launch_kron_step(fd_ctx* ctx, const fd_matrix* M, int mode, const Step
 
 template <typename T, int NB>
 fd_status launch_step(fd_ctx* ctx, const fd_matrix* M, int mode, const StepArgs<T>& s) {
-  if (M->kron) return launch_kron_step<T, NB>(ctx, M, mode, s);
+  if constexpr (std::is_same_v<T, ff>) {
+    if (M->kron) return set_err(ctx, FD_ERR_ARG, "float-float sweeps need a stored matrix (kron = 0)");
+  } else {
+    if (M->kron) return launch_kron_step<T, NB>(ctx, M, mode, s);
+  }
   using L = Layout<T, NB>;
   SellArgs<T> A;
   A.chunk_ptr = M->chunk_ptr; A.row_len = M->row_len; A.col = M->col; A.D = M->D; A.C = M->C;
-  if constexpr (sizeof(T) == 8) A.val = (const T*)M->val; else A.val = (const T*)M->val32;
+  if constexpr (std::is_same_v<T, double>) A.val = M->val;
+  else if constexpr (std::is_same_v<T, float>) A.val = M->val32;
+  else A.val = reinterpret_cast<const ff*>(M->valff);
   constexpr int SW = step_warps<T>();
   const int64_t rows_per_block = (int64_t)SW * L::RPW;
   const unsigned grid = (unsigned)cdiv(M->D, rows_per_block);
@@ -144,7 +153,7 @@ fd_status step_dispatch(fd_ctx* ctx, const fd_matrix* M, int nb, int mode, const
 }
 
 bool nb_ok(fd_prec prec, int nb) {
-  if (prec == FD_F64) return nb == 2 || nb == 4 || nb == 8 || nb == 16 || nb == 32 || nb == 64 || nb == 128;
+  if (prec == FD_F64 || prec == FD_FF) return nb == 2 || nb == 4 || nb == 8 || nb == 16 || nb == 32 || nb == 64 || nb == 128;
   return nb == 4 || nb == 8 || nb == 16 || nb == 32 || nb == 64 || nb == 128;
 }
 
@@ -428,13 +437,17 @@ fd_status filter(fd_ctx* ctx, const fd_matrix* M, fd_prec prec, void* V, int64_t
   if (prec == FD_F64)
     return filter_t<double>(ctx, M, (double*)V, ldv, nb, degree, mu, alpha, beta, (double*)W1,
                             (double*)W2, ldw, bytes_out);
+  if (prec == FD_FF)
+    return filter_t<ff>(ctx, M, (ff*)V, ldv, nb, degree, mu, alpha, beta, (ff*)W1, (ff*)W2, ldw,
+                        bytes_out);
   return filter_t<float>(ctx, M, (float*)V, ldv, nb, degree, mu, alpha, beta, (float*)W1,
                          (float*)W2, ldw, bytes_out);
 }
 
 fd_status spmmv(fd_ctx* ctx, const fd_matrix* M, fd_prec prec, const void* X, int64_t ldx,
                 void* Y, int64_t ldy, int nb, bool original_order) {
-  const size_t es = prec == FD_F64 ? 8 : 4;
+  const size_t es = prec == FD_F32 ? 4 : 8;
+  const bool wide = prec != FD_F32;  // double or float-float: 8-byte elements, permuted as such
   const bool ident = M->identity != 0 || !original_order;
   const void* xs = X;
   int64_t ldxs = ldx;
@@ -447,20 +460,24 @@ fd_status spmmv(fd_ctx* ctx, const fd_matrix* M, fd_prec prec, const void* X, in
     ldxs = nb;
     ys = (char*)p + es * M->D * nb;
     ldys = nb;
-    if (prec == FD_F64) FD_TRY(permute<double>(ctx, M, (const double*)X, ldx, (double*)xs, nb, nb, true));
+    if (wide) FD_TRY(permute<double>(ctx, M, (const double*)X, ldx, (double*)xs, nb, nb, true));
     else FD_TRY(permute<float>(ctx, M, (const float*)X, ldx, (float*)xs, nb, nb, true));
   }
   if (prec == FD_F64) {
     StepArgs<double> s{};
     s.X = (const double*)xs; s.ldx = ldxs; s.Y = (double*)ys; s.ldy = ldys; s.c_ax = 1.0; s.c_x = 0.0;
     FD_TRY(step_dispatch<double>(ctx, M, nb, MODE_SPMMV, s));
+  } else if (prec == FD_FF) {
+    StepArgs<ff> s{};
+    s.X = (const ff*)xs; s.ldx = ldxs; s.Y = (ff*)ys; s.ldy = ldys; s.c_ax = ff(1); s.c_x = ff(0);
+    FD_TRY(step_dispatch<ff>(ctx, M, nb, MODE_SPMMV, s));
   } else {
     StepArgs<float> s{};
     s.X = (const float*)xs; s.ldx = ldxs; s.Y = (float*)ys; s.ldy = ldys; s.c_ax = 1.0f; s.c_x = 0.0f;
     FD_TRY(step_dispatch<float>(ctx, M, nb, MODE_SPMMV, s));
   }
   if (!ident) {
-    if (prec == FD_F64) FD_TRY(permute<double>(ctx, M, (const double*)ys, nb, (double*)Y, ldy, nb, false));
+    if (wide) FD_TRY(permute<double>(ctx, M, (const double*)ys, nb, (double*)Y, ldy, nb, false));
     else FD_TRY(permute<float>(ctx, M, (const float*)ys, nb, (float*)Y, ldy, nb, false));
   }
   return FD_OK;
@@ -499,10 +516,10 @@ fd_status fd_filter(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, void* V, int6
   if (!ctx) return FD_ERR_ARG;
   ctx->err.clear();
   if (!A || !V || !mu || !W1 || !W2) return set_err(ctx, FD_ERR_ARG, "null argument");
-  if (prec != FD_F64 && prec != FD_F32) return set_err(ctx, FD_ERR_ARG, "bad precision");
+  if (prec != FD_F64 && prec != FD_F32 && prec != FD_FF) return set_err(ctx, FD_ERR_ARG, "bad precision");
   if (!nb_ok(prec, nb)) return set_err(ctx, FD_ERR_ARG, "unsupported nb %d", nb);
   if (degree < 2) return set_err(ctx, FD_ERR_ARG, "degree must be >= 2 (Alg. 2)");
-  const size_t es = prec == FD_F64 ? 8 : 4;
+  const size_t es = prec == FD_F32 ? 4 : 8;
   if (ldv < nb || ldw < nb || (ldv * es) % 16 || (ldw * es) % 16 || !aligned16(V) ||
       !aligned16(W1) || !aligned16(W2))
     return set_err(ctx, FD_ERR_ARG, "ld must be >= nb with 16-byte aligned rows and pointers");
@@ -519,9 +536,9 @@ fd_status fd_spmmv(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, const void* X,
   if (!ctx) return FD_ERR_ARG;
   ctx->err.clear();
   if (!A || !X || !Y) return set_err(ctx, FD_ERR_ARG, "null argument");
-  if (prec != FD_F64 && prec != FD_F32) return set_err(ctx, FD_ERR_ARG, "bad precision");
+  if (prec != FD_F64 && prec != FD_F32 && prec != FD_FF) return set_err(ctx, FD_ERR_ARG, "bad precision");
   if (!nb_ok(prec, nb)) return set_err(ctx, FD_ERR_ARG, "unsupported nb %d", nb);
-  const size_t es = prec == FD_F64 ? 8 : 4;
+  const size_t es = prec == FD_F32 ? 4 : 8;
   if (ldx < nb || ldy < nb || (ldx * es) % 16 || (ldy * es) % 16 || !aligned16(X) || !aligned16(Y))
     return set_err(ctx, FD_ERR_ARG, "ld must be >= nb with 16-byte aligned rows and pointers");
   if (X == Y) return set_err(ctx, FD_ERR_ARG, "X and Y must not alias");

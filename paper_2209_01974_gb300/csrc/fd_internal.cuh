@@ -45,6 +45,7 @@ struct fd_matrix {
   int32_t* col = nullptr;        // nnz_sell, SELL column indices
   double* val = nullptr;         // nnz_sell
   float* val32 = nullptr;        // nnz_sell
+  float* valff = nullptr;        // 2 nnz_sell: float-float (hi, lo) pairs of val
   int64_t* perm = nullptr;       // D: SELL row -> original row
   int64_t* iperm = nullptr;      // D: original row -> SELL row
   uint8_t* diag_added = nullptr; // D (SELL order): 1 if the diagonal was not in the input
@@ -73,6 +74,15 @@ struct fd_matrix {
   double kdn_val[2] = {0, 0};
   float kdn_val32[2] = {0, 0};
   int kmax_up = 0;                // most up hops of one state
+  // the down-spin tables cut into row tiles of ktile_rows rows for the
+  // bulk-copy pipelined kernel: per tile t a 16-byte aligned record at byte
+  // ktile_off[t] of ktile: bits (ktile_rows x uint32), row starts relative to
+  // the tile's first entry (ktile_rows + 1 x uint16, padded to 16 bytes), then
+  // the tile's 16-bit entries (padded to 16 bytes)
+  uint8_t* ktile = nullptr;
+  uint32_t* ktile_off = nullptr;  // ktile_n + 1
+  int ktile_rows = 0, ktile_n = 0;
+  uint32_t ktile_max = 0;         // largest record
 };
 
 namespace fdi {
@@ -134,6 +144,8 @@ fd_status kron_filter(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, void* V, in
                       void* W1, void* W2, int64_t ldw, double* bytes_out);
 // the panel kernel's tables of A (after the per-species tables exist)
 fd_status kron_panel_tables(fd_ctx* ctx, fd_matrix* A, double t);
+// rows per tile of the pipelined matrix-free kernel (its consumer threads)
+constexpr int KRON_TILE_ROWS = 192;
 // nb = 1 SpMV in SELL order, FP64: y = A x (x, y dense vectors in SELL order)
 fd_status spmv1(fd_ctx* ctx, const fd_matrix* A, const double* x, double* y);
 // KPM Chebyshev iteration with moment epilogue (fd_filter.cu)
@@ -189,6 +201,11 @@ fd_status copy_cols_f64_to_f32(fd_ctx* ctx, const double* src, int64_t lds, floa
                                int64_t ldd, int64_t D, int n);
 fd_status copy_cols_f32_to_f64(fd_ctx* ctx, const float* src, int64_t lds, double* dst,
                                int64_t ldd, int64_t D, int n);
+// FP64 <-> float-float blocks (ld in elements; a float-float element is 2 floats)
+fd_status copy_cols_f64_to_ff(fd_ctx* ctx, const double* src, int64_t lds, float* dst, int64_t ldd,
+                              int64_t D, int n);
+fd_status copy_cols_ff_to_f64(fd_ctx* ctx, const float* src, int64_t lds, double* dst, int64_t ldd,
+                              int64_t D, int n);
 
 // ---- Lehmann bounds (fd_lehmann.cu) -----------------------------------------
 // eigenvalues (device, ascending) of the pencil A1 x = mu A2 x (A1, A2 destroyed);

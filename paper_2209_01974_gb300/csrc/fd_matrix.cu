@@ -299,6 +299,17 @@ __global__ void k_kron_fill(int L, int N, int periodic, double t, int64_t dim, c
   }
 }
 
+// float-float copy of the values: hi the nearest float, lo the nearest float
+// to the remainder (exact in FP64), so hi + lo is within 2^-48 of the value
+__global__ void k_split_ff(const double* val, int64_t n, float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = val[i];
+  const float hi = __double2float_rn(v);
+  out[2 * i] = hi;
+  out[2 * i + 1] = __double2float_rn(v - (double)hi);
+}
+
 __global__ void k_hubbard_fill(HubbardP p, const int64_t* rowptr, int32_t* col, double* val) {
   int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= p.D) return;
@@ -646,6 +657,11 @@ fd_status sell_from_device_csr(fd_ctx* ctx, fd_matrix* A, const int64_t* d_rowpt
       d_rowptr, d_col, d_val, A->perm, A->iperm, A->chunk_ptr, A->row_len, D, C, A->n_chunks,
       A->col, A->val, A->val32);
   FD_LAUNCHED(ctx);
+  FD_CUDA(ctx, cudaMalloc(&A->valff, 2 * sizeof(float) * std::max<int64_t>(1, nnz_sell)));
+  if (nnz_sell > 0) {
+    k_split_ff<<<(unsigned)cdiv(nnz_sell, T), T, 0, st>>>(A->val, nnz_sell, A->valff);
+    FD_LAUNCHED(ctx);
+  }
 
   // Gershgorin interval and longest row
   const int PB = 256;
@@ -1026,13 +1042,14 @@ fd_status fd_matrix_free(fd_matrix* A) {
   cudaSetDevice(A->device);
   cudaDeviceSynchronize();
   cudaFree(A->chunk_ptr); cudaFree(A->row_len); cudaFree(A->col); cudaFree(A->val);
-  cudaFree(A->val32); cudaFree(A->perm); cudaFree(A->iperm); cudaFree(A->diag_added);
+  cudaFree(A->val32); cudaFree(A->valff); cudaFree(A->perm); cudaFree(A->iperm); cudaFree(A->diag_added);
   for (int sp = 0; sp < 2; ++sp) {
     cudaFree(A->kbits[sp]); cudaFree(A->kptr[sp]); cudaFree(A->kcol[sp]);
     cudaFree(A->kval[sp]); cudaFree(A->kval32[sp]);
   }
   cudaFree(A->kdiag); cudaFree(A->kdiag32);
   cudaFree(A->korder); cudaFree(A->kdn_ptr); cudaFree(A->kdn_ent); cudaFree(A->kdn_ent16);
+  cudaFree(A->ktile); cudaFree(A->ktile_off);
   delete A;
   return FD_OK;
 }

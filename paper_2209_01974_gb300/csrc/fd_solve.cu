@@ -303,7 +303,15 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
     return set_err(ctx, FD_ERR_ARG, "need finite a <= b and tol > 0");
   if (nb != 2 && nb != 4 && nb != 8 && nb != 16 && nb != 32 && nb != 64 && nb != 128)
     return set_err(ctx, FD_ERR_ARG, "nb must be 2, 4, ..., 128");
+  if (opt.precision != FD_F64 && opt.precision != FD_F32 && opt.precision != FD_FF)
+    return set_err(ctx, FD_ERR_ARG, "bad precision");
+  if (opt.finish != FD_FINISH_F64 && opt.finish != FD_FINISH_FF)
+    return set_err(ctx, FD_ERR_ARG, "finish must be FD_FINISH_F64 or FD_FINISH_FF");
   if (opt.precision == FD_F32 && nb < 4) return set_err(ctx, FD_ERR_ARG, "FP32 sweeps need nb >= 4");
+  // float-float sweeps: the FD_FF form, or the FD_F32 form's finish
+  const bool ff_sweeps = opt.precision == FD_FF || (opt.precision == FD_F32 && opt.finish == FD_FINISH_FF);
+  if (ff_sweeps && A && A->kron)
+    return set_err(ctx, FD_ERR_ARG, "float-float sweeps need a stored matrix (kron = 0)");
   if (degree < 2) return set_err(ctx, FD_ERR_ARG, "degree must be >= 2 (Alg. 2)");
   if (opt.intervals != FD_INTERVALS_RITZ && opt.intervals != FD_INTERVALS_LEHMANN)
     return set_err(ctx, FD_ERR_ARG, "intervals must be FD_INTERVALS_RITZ or FD_INTERVALS_LEHMANN");
@@ -336,6 +344,12 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
   if (opt.precision == FD_F32) {
     FD_TRY(workspace(ctx, "solve_W32", sizeof(float) * 3 * D * nb, &p));
     V32 = (float*)p; W132 = V32 + D * nb; W232 = W132 + D * nb;
+  }
+  // float-float bundle (2 floats per element); its recurrence vectors reuse W1, W2
+  float* Vff = nullptr;
+  if (ff_sweeps) {
+    FD_TRY(workspace(ctx, "solve_Wff", sizeof(float) * 2 * D * nb, &p));
+    Vff = (float*)p;
   }
   FD_TRY(workspace(ctx, "solve_small", sizeof(double) * 2 * ns + sizeof(int) * ns + 64, &p));
   double* th_dev = (double*)p;
@@ -374,6 +388,7 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
     wl = ck->window_l; wr = ck->window_r; n = ck->degree;
     use_f32 = ck->use_f32 != 0; prev_max = ck->prev_max; stall = ck->stall; it = ck->iteration;
     res->n_spmmv = ck->n_spmmv; res->n_spmmv_f32 = ck->n_spmmv_f32; res->filter_bytes = ck->filter_bytes;
+    res->n_spmmv_ff = ck->n_spmmv_ff;
     FD_CUDA(ctx, cudaMemcpyAsync(V, Vck, sizeof(double) * D * ns, cudaMemcpyDeviceToDevice, st));
   }
   const double tau = 0.5 * (a + b);
@@ -400,7 +415,7 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
     }
     if (opt.verbose)
       fprintf(stderr, "fd it %d degree %d window [%.6g, %.6g] conv %d/%d max_resid %.3e %s\n", it, n,
-              wl, wr, nconv, n_target, maxr, use_f32 ? "f32" : "f64");
+              wl, wr, nconv, n_target, maxr, use_f32 ? "f32" : ff_sweeps ? "ff" : "f64");
     if (nconv == n_target) { done = true; ++it; break; }
     if (it == max_outer - 1) { ++it; break; }  // keep V = Ritz vectors of the last step
     // precision switch: FP32 sweeps until their floor or a stall (two
@@ -451,6 +466,10 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
         FD_TRY(copy_cols_f64_to_f32(ctx, V + j, ns, V32, nb, D, nb));
         FD_TRY(filter(ctx, A, FD_F32, V32, nb, nb, n, mu.data(), alpha, beta, W132, W232, nb, &bytes));
         FD_TRY(copy_cols_f32_to_f64(ctx, V32, nb, V + j, ns, D, nb));
+      } else if (ff_sweeps) {
+        FD_TRY(copy_cols_f64_to_ff(ctx, V + j, ns, Vff, nb, D, nb));
+        FD_TRY(filter(ctx, A, FD_FF, Vff, nb, nb, n, mu.data(), alpha, beta, W1, W2, nb, &bytes));
+        FD_TRY(copy_cols_ff_to_f64(ctx, Vff, nb, V + j, ns, D, nb));
       } else {
         FD_TRY(filter(ctx, A, FD_F64, V + j, ns, nb, n, mu.data(), alpha, beta, W1, W2, nb, &bytes));
       }
@@ -459,6 +478,7 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
     res->filter_bytes += bytes;
     res->n_spmmv += n;
     if (use_f32) res->n_spmmv_f32 += n;
+    else if (ff_sweeps) res->n_spmmv_ff += n;
     if (ck && it + 1 == it_stop && it + 1 < max_outer) {  // pause after this filter application
       ++it;
       paused = true;
@@ -472,6 +492,7 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
     ck->lam_l = lam_l; ck->lam_r = lam_r; ck->widen = widen; ck->norm_h = normH;
     ck->window_l = wl; ck->window_r = wr; ck->prev_max = prev_max;
     ck->n_spmmv = res->n_spmmv; ck->n_spmmv_f32 = res->n_spmmv_f32; ck->filter_bytes = res->filter_bytes;
+    ck->n_spmmv_ff = res->n_spmmv_ff;
     ck->D = D; ck->ns = ns; ck->seed = opt.seed; ck->converged = 0;
   }
   // outputs: the N_t pairs nearest tau, ascending

@@ -97,6 +97,10 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   return p;
 }
 
+// read-only load of one matrix value (float-float values have their own)
+template <typename T>
+__device__ __forceinline__ T ldg_val(const T* p) { return __ldg(p); }
+
 template <typename T>
 struct SellArgs {
   const int64_t* chunk_ptr;
@@ -167,7 +171,7 @@ __device__ __forceinline__ void row_product(const SellArgs<T>& A, const T* __res
 #pragma unroll
     for (int u = 0; u < BATCH; ++u) {
       c[u] = __ldg(cp + u * C);
-      a[u] = __ldg(vp + u * C);
+      a[u] = ldg_val(vp + u * C);
     }
     if (!active) { c[0] = 0; a[0] = T(0); }
 #pragma unroll
@@ -195,7 +199,7 @@ __device__ __forceinline__ void row_product(const SellArgs<T>& A, const T* __res
 #pragma unroll
     for (int u = 0; u < BATCH; ++u) {
       c[u] = __ldg(cp + (j0 + u) * C);
-      a[u] = __ldg(vp + (j0 + u) * C);
+      a[u] = ldg_val(vp + (j0 + u) * C);
     }
 #pragma unroll
     for (int u = 0; u < BATCH; ++u) {
