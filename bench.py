@@ -581,7 +581,7 @@ def run_kernel_only(prec, workload="stencil", nb=NB, degree=12, reps=5):
     import torch
 
     import paper_2209_01974_gb300 as fd
-    dt = torch.float64 if prec == "f64" else torch.float32
+    dt = torch.float32 if prec == "f32" else torch.float64  # float-float blocks are split from FP64
     ctx = fd.fd_create(0)
     A = fd.fd_build_matrix(ctx, KERNEL_WORKLOADS[workload])
     D, nnz = A.D, A.info["nnz"]

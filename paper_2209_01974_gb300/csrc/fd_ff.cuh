@@ -64,8 +64,21 @@ __device__ __forceinline__ ff operator*(ff a, ff b) {
   fast_two_sum(p, e, r.hi, r.lo);
   return r;
 }
-// c + a * b (product and sum as above)
-__device__ __forceinline__ ff fma(ff a, ff b, ff c) { return a * b + c; }
+// c + a * b for running sums (the row sums of the SpMMV): the exact product
+// of the high parts (TwoProd) and the exact sum of it with c.hi (TwoSum) give
+// the new high part; every remaining term (both rounding errors, the cross
+// products, c.lo) is added in plain FP32 to the low part, which is left
+// unnormalised.  The low part then carries an error of a few u^2 of the terms
+// summed so far, as in the normalised sum; the pair is renormalised by the next
+// product or sum (12 FP32 operations instead of 18).
+__device__ __forceinline__ ff fma(ff a, ff b, ff c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  float s, t;
+  two_sum(c.hi, p, s, t);
+  return ff(s, __fadd_rn(__fadd_rn(t, e), c.lo));
+}
 
 // read-only loads of one value (matrix entries)
 __device__ __forceinline__ ff ldg_val(const ff* p) {

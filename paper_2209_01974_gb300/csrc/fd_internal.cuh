@@ -74,15 +74,6 @@ struct fd_matrix {
   double kdn_val[2] = {0, 0};
   float kdn_val32[2] = {0, 0};
   int kmax_up = 0;                // most up hops of one state
-  // the down-spin tables cut into row tiles of ktile_rows rows for the
-  // bulk-copy pipelined kernel: per tile t a 16-byte aligned record at byte
-  // ktile_off[t] of ktile: bits (ktile_rows x uint32), row starts relative to
-  // the tile's first entry (ktile_rows + 1 x uint16, padded to 16 bytes), then
-  // the tile's 16-bit entries (padded to 16 bytes)
-  uint8_t* ktile = nullptr;
-  uint32_t* ktile_off = nullptr;  // ktile_n + 1
-  int ktile_rows = 0, ktile_n = 0;
-  uint32_t ktile_max = 0;         // largest record
 };
 
 namespace fdi {
@@ -144,8 +135,6 @@ fd_status kron_filter(fd_ctx* ctx, const fd_matrix* A, fd_prec prec, void* V, in
                       void* W1, void* W2, int64_t ldw, double* bytes_out);
 // the panel kernel's tables of A (after the per-species tables exist)
 fd_status kron_panel_tables(fd_ctx* ctx, fd_matrix* A, double t);
-// rows per tile of the pipelined matrix-free kernel (its consumer threads)
-constexpr int KRON_TILE_ROWS = 192;
 // nb = 1 SpMV in SELL order, FP64: y = A x (x, y dense vectors in SELL order)
 fd_status spmv1(fd_ctx* ctx, const fd_matrix* A, const double* x, double* y);
 // KPM Chebyshev iteration with moment epilogue (fd_filter.cu)

@@ -546,40 +546,6 @@ fd_status kron_panel_tables(fd_ctx* ctx, fd_matrix* A, double t) {
     FD_CUDA(ctx, cudaMalloc(&A->kdn_ent16, sizeof(uint16_t) * ent16.size()));
     FD_CUDA(ctx, cudaMemcpyAsync(A->kdn_ent16, ent16.data(), sizeof(uint16_t) * ent16.size(),
                                  cudaMemcpyHostToDevice, st));
-    // the same tables cut into row tiles, one bulk copy per tile
-    const int TR = KRON_TILE_ROWS;
-    const int nt = (int)cdiv(dd, TR);
-    auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-    std::vector<uint32_t> toff(nt + 1, 0);
-    std::vector<uint8_t> blob;
-    std::vector<uint32_t> bits_dn(dd);
-    FD_CUDA(ctx, cudaMemcpyAsync(bits_dn.data(), A->kbits[1], sizeof(uint32_t) * dd, cudaMemcpyDeviceToHost, st));
-    FD_CUDA(ctx, cudaStreamSynchronize(st));
-    uint32_t tmax = 0;
-    for (int t = 0; t < nt; ++t) {
-      const int64_t d0 = (int64_t)t * TR, rows = std::min<int64_t>(TR, dd - d0);
-      const size_t bits_b = pad16(sizeof(uint32_t) * TR), ptr_b = pad16(sizeof(uint16_t) * (TR + 1));
-      const uint32_t e0 = ptr32[d0], e1 = ptr32[d0 + rows];
-      const size_t rec = bits_b + ptr_b + pad16(sizeof(uint16_t) * (e1 - e0));
-      std::vector<uint8_t> r(rec, 0);
-      uint32_t* rb = (uint32_t*)r.data();
-      uint16_t* rp = (uint16_t*)(r.data() + bits_b);
-      uint16_t* re = (uint16_t*)(r.data() + bits_b + ptr_b);
-      for (int64_t q = 0; q < rows; ++q) rb[q] = bits_dn[d0 + q];
-      for (int64_t q = 0; q <= rows; ++q) rp[q] = (uint16_t)(ptr32[d0 + q] - e0);
-      for (uint32_t k = e0; k < e1; ++k) re[k - e0] = ent16[k];
-      toff[t] = (uint32_t)blob.size();
-      blob.insert(blob.end(), r.begin(), r.end());
-      tmax = std::max<uint32_t>(tmax, (uint32_t)rec);
-    }
-    toff[nt] = (uint32_t)blob.size();
-    FD_CUDA(ctx, cudaMalloc(&A->ktile, std::max<size_t>(blob.size(), 16)));
-    FD_CUDA(ctx, cudaMalloc(&A->ktile_off, sizeof(uint32_t) * (nt + 1)));
-    FD_CUDA(ctx, cudaMemcpyAsync(A->ktile, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
-    FD_CUDA(ctx, cudaMemcpyAsync(A->ktile_off, toff.data(), sizeof(uint32_t) * (nt + 1), cudaMemcpyHostToDevice, st));
-    A->ktile_rows = TR;
-    A->ktile_n = nt;
-    A->ktile_max = tmax;
   }
   FD_CUDA(ctx, cudaStreamSynchronize(st));
   return FD_OK;

@@ -1049,7 +1049,6 @@ fd_status fd_matrix_free(fd_matrix* A) {
   }
   cudaFree(A->kdiag); cudaFree(A->kdiag32);
   cudaFree(A->korder); cudaFree(A->kdn_ptr); cudaFree(A->kdn_ent); cudaFree(A->kdn_ent16);
-  cudaFree(A->ktile); cudaFree(A->ktile_off);
   delete A;
   return FD_OK;
 }

@@ -59,7 +59,7 @@ def test_split_round_trip(fd, ctx):
     import torch
     rng = np.random.default_rng(1)
     x = rng.standard_normal((1000, 8)) * np.exp(rng.uniform(-20, 20, (1000, 8)))
-    x[:, 0] = np.round(x[:, 0] * 2.0 ** 20) / 2.0 ** 20  # few significant bits: exact
+    x[:, 0] = rng.integers(-2 ** 40, 2 ** 40, 1000) * 2.0 ** -30  # at most 41 significant bits: exact
     X = torch.from_numpy(x).cuda()
     ff = _ff_block(fd, ctx, X)
     pairs = ff.cpu().numpy().astype(np.float64)
