@@ -281,10 +281,9 @@ fd_status fd_orthonormalize(fd_ctx* ctx, double* V, int64_t D, int ns,
  * that every GPU loading the library holds until the process exits.
  *   ns      at most 256 (larger blocks return FD_ERR_ARG)
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array: calls that overlap on the GPU
- * (other host threads, other streams) race and must be serialised by the
- * caller.  Every product runs in FP64 arithmetic (the tensor-core products
+ * device, with that device current).  Every call shares the one array: calls
+ * that overlap on the GPU (other host threads, other streams) race and must
+ * be serialised by the caller.  Every product runs in FP64 arithmetic (the tensor-core products
  * need digit workspaces), whatever fd_set_gemm_mode selected, and the call
  * synchronises the context's stream once per pass (the pivot check).  It
  * never calls cudaMalloc or cudaFree and leaves the context's workspaces
