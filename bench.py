@@ -812,7 +812,7 @@ def main():
     ap.add_argument("--tts-nt", type=int, default=32)
     ap.add_argument("--tts-half-width", type=float, default=0.002)
     ap.add_argument("--tts-forms", default="f64,f32,f32_learned")
-    ap.add_argument("--tts-forms-bench", default="f64,f64_lehmann,f32,f32_learned",
+    ap.add_argument("--tts-forms-bench", default="f64,f64_lehmann,f32,f32_ff,f32_learned,f32_ff_learned",
                     help="forms of the time-to-solution block of the default bench line")
     ap.add_argument("--no-tts", action="store_true", help="skip the L=48 time-to-solution block")
     ap.add_argument("--no-config3", action="store_true", help="skip the 14-site Hubbard ring sweep")

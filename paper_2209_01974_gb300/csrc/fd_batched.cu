@@ -67,16 +67,21 @@ struct BTask {
   int inst, bundle;
 };
 
+// The tasks (bundles) of the instances still active, rewritten by the host
+// before every outer iteration: ordered by their instance's filter degree,
+// largest first, so that the tasks still filtering at degree step k are a
+// prefix of the list and a step touches only their rows.
 struct BatchArgs {
   const BInst* inst;
   BParams* par;
   const BTask* task;
   const int64_t* task_off;  // n_tasks + 1 row offsets (each task padded to RPW rows)
+  const int* task_deg;      // n_tasks filter degrees, non-increasing
+  const int* n_tasks;       // tasks in the list this iteration
   const double* mu;
   const int* kmax;          // largest degree this iteration
-  int n_tasks;
   int nb;
-  int spmmv_only;           // 1: AV = A V for all bundles, one pass, no barrier
+  int spmmv_only;           // 1: AV = A V for all listed bundles, one pass, no barrier
 };
 
 constexpr int GSLICES = 8;   // Gram row slices per instance
@@ -206,20 +211,25 @@ __device__ __forceinline__ void batched_row_group_ff(const BatchArgs& b, int t, 
 template <int NB, bool FF>
 __global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
   using L = Layout<double, NB>;
-  extern __shared__ int64_t s_off[];  // n_tasks + 1
-  for (int i = threadIdx.x; i <= b.n_tasks; i += blockDim.x) s_off[i] = b.task_off[i];
+  extern __shared__ int64_t s_off[];  // n_tasks + 1 offsets, then n_tasks degrees
+  const int nt = *b.n_tasks;
+  int* s_deg = reinterpret_cast<int*>(s_off + nt + 1);
+  for (int i = threadIdx.x; i <= nt; i += blockDim.x) s_off[i] = b.task_off[i];
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) s_deg[i] = b.task_deg[i];
   __syncthreads();
-  const int64_t total = s_off[b.n_tasks];
-  const int64_t ngroups = total / L::RPW;
   const int warps = blockDim.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
   const int64_t nw = (int64_t)gridDim.x * warps;
   const int kmax = b.spmmv_only ? 1 : *b.kmax;
   cg::grid_group grid = cg::this_grid();
+  int cut = nt;  // tasks still filtering: the prefix with degree >= k
   for (int k = 1; k <= kmax; ++k) {
+    if (!b.spmmv_only)
+      while (cut > 0 && s_deg[cut - 1] < k) --cut;
+    const int64_t ngroups = s_off[cut] / L::RPW;
     for (int64_t g = gw; g < ngroups; g += nw) {
       const int64_t r0 = g * L::RPW;
-      int lo = 0, hi = b.n_tasks - 1;  // last task with s_off[t] <= r0
+      int lo = 0, hi = cut - 1;  // last task with s_off[t] <= r0
       while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (s_off[mid] <= r0) lo = mid; else hi = mid - 1;
@@ -608,6 +618,13 @@ struct Batch {
   int n = 0, nb = 0, warps = WARPS, ns_max = 0;
   bool f32 = false;  // FP32 sweeps available (the FP32 form)
   bool ff = false;   // float-float sweeps possible (FF form or float-float finish)
+  int rpw = 1;       // row granule of a task
+  size_t n_tasks_all = 0;
+  int* d_tdeg = nullptr;
+  int* d_ntask = nullptr;
+  BTask* h_task_p = nullptr;   // pinned mirrors of the per-iteration task list
+  int64_t* h_off_p = nullptr;
+  int* h_tdeg_p = nullptr;
   std::vector<BInst> h_inst;
   std::vector<BTask> h_task;
   std::vector<int64_t> h_off;
@@ -636,7 +653,28 @@ struct Batch {
     cudaFreeHost(h_mu);
     cudaFreeHost(h_kmax);
     cudaFreeHost(h_out);
+    cudaFreeHost(h_task_p);
+    cudaFreeHost(h_off_p);
+    cudaFreeHost(h_tdeg_p);
   }
+  // the tasks of the active instances, largest degree first (h_par's degrees)
+  void list_tasks() {
+    std::vector<int> order;
+    for (int i = 0; i < n; ++i)
+      if (h_par[i].active) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return h_par[x].degree > h_par[y].degree; });
+    size_t t = 0;
+    h_off_p[0] = 0;
+    for (int i : order)
+      for (int bnd = 0; bnd < h_inst[i].ns / nb; ++bnd, ++t) {
+        h_task_p[t] = BTask{i, bnd};
+        h_tdeg_p[t] = h_par[i].degree;
+        h_off_p[t + 1] = h_off_p[t] + cdiv(h_inst[i].A.D, rpw) * rpw;
+      }
+    *h_ntask = (int)t;
+  }
+  int* h_ntask = nullptr;
 };
 
 template <int NB>
@@ -719,16 +757,20 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
   B.h_off.assign(B.h_task.size() + 1, 0);
   for (size_t t = 0; t < B.h_task.size(); ++t)
     B.h_off[t + 1] = B.h_off[t] + cdiv(B.h_inst[B.h_task[t].inst].A.D, rpw) * rpw;
+  B.rpw = rpw;
+  B.n_tasks_all = B.h_task.size();
+  const size_t nta = B.n_tasks_all;
   void* p;
-  FD_TRY(workspace(ctx, "batch_desc", sizeof(BInst) * n + sizeof(BParams) * n +
-                                          sizeof(BTask) * B.h_task.size() +
-                                          sizeof(int64_t) * (B.h_off.size() + 1) + 64, &p));
+  FD_TRY(workspace(ctx, "batch_desc", sizeof(BInst) * n + sizeof(BParams) * n + sizeof(BTask) * nta +
+                                          sizeof(int64_t) * (nta + 1) + sizeof(int) * (nta + 1) + 64, &p));
   char* c = (char*)p;
   B.d_inst = (BInst*)c; c += sizeof(BInst) * n;
   B.d_par = (BParams*)c; c += sizeof(BParams) * n;
-  B.d_task = (BTask*)c; c += sizeof(BTask) * B.h_task.size();
+  B.d_task = (BTask*)c; c += sizeof(BTask) * nta;
   c = (char*)(((uintptr_t)c + 15) & ~(uintptr_t)15);
-  B.d_off = (int64_t*)c;
+  B.d_off = (int64_t*)c; c += sizeof(int64_t) * (nta + 1);
+  B.d_tdeg = (int*)c; c += sizeof(int) * nta;
+  B.d_ntask = (int*)c;
   B.mu_cap = mu_cap;
   FD_TRY(workspace(ctx, "batch_mu", sizeof(double) * mu_cap + 64, &p));
   B.d_mu = (double*)p;
@@ -740,10 +782,21 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
   FD_CUDA(ctx, cudaMallocHost(&B.h_mu, sizeof(double) * mu_cap));
   FD_CUDA(ctx, cudaMallocHost(&B.h_kmax, sizeof(int)));
   FD_CUDA(ctx, cudaMallocHost(&B.h_out, sizeof(double) * 2 * n * B.ns_max + sizeof(BParams) * n));
+  FD_CUDA(ctx, cudaMallocHost(&B.h_task_p, sizeof(BTask) * nta));
+  FD_CUDA(ctx, cudaMallocHost(&B.h_off_p, sizeof(int64_t) * (nta + 1)));
+  FD_CUDA(ctx, cudaMallocHost(&B.h_tdeg_p, sizeof(int) * std::max<size_t>(nta, 1)));
+  FD_CUDA(ctx, cudaMallocHost(&B.h_ntask, sizeof(int)));
+  // until the caller sets degrees: every task, all degrees 0
+  std::copy(B.h_task.begin(), B.h_task.end(), B.h_task_p);
+  std::copy(B.h_off.begin(), B.h_off.end(), B.h_off_p);
+  std::fill(B.h_tdeg_p, B.h_tdeg_p + nta, 0);
+  *B.h_ntask = (int)nta;
+  FD_CUDA(ctx, cudaMemcpyAsync(B.d_tdeg, B.h_tdeg_p, sizeof(int) * nta, cudaMemcpyHostToDevice, ctx->stream));
+  FD_CUDA(ctx, cudaMemcpyAsync(B.d_ntask, B.h_ntask, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   // persistent filter grid: every CTA resident
   const void* kf = filter_kernel_for(nb, B.ff);
   if (!kf) return set_err(ctx, FD_ERR_ARG, "batched filter supports nb = 2 .. 64");
-  B.smem_filter = sizeof(int64_t) * (B.h_task.size() + 1);
+  B.smem_filter = sizeof(int64_t) * (nta + 1) + sizeof(int) * nta;
   if (B.smem_filter > 48 * 1024)
     FD_CUDA(ctx, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem_filter));
   int per_sm = 0;
@@ -753,10 +806,22 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
   return FD_OK;
 }
 
+// the host's task list (Batch::list_tasks) to the device, on the context's stream
+fd_status copy_tasks(fd_ctx* ctx, Batch& B) {
+  cudaStream_t st = ctx->stream;
+  const size_t nta = B.n_tasks_all;
+  FD_CUDA(ctx, cudaMemcpyAsync(B.d_task, B.h_task_p, sizeof(BTask) * nta, cudaMemcpyHostToDevice, st));
+  FD_CUDA(ctx, cudaMemcpyAsync(B.d_off, B.h_off_p, sizeof(int64_t) * (nta + 1), cudaMemcpyHostToDevice, st));
+  FD_CUDA(ctx, cudaMemcpyAsync(B.d_tdeg, B.h_tdeg_p, sizeof(int) * nta, cudaMemcpyHostToDevice, st));
+  FD_CUDA(ctx, cudaMemcpyAsync(B.d_ntask, B.h_ntask, sizeof(int), cudaMemcpyHostToDevice, st));
+  return FD_OK;
+}
+
 fd_status launch_filter(fd_ctx* ctx, Batch& B, int spmmv_only) {
   BatchArgs a;
   a.inst = B.d_inst; a.par = B.d_par; a.task = B.d_task; a.task_off = B.d_off; a.mu = B.d_mu;
-  a.kmax = B.d_kmax; a.n_tasks = (int)B.h_task.size(); a.nb = B.nb; a.spmmv_only = spmmv_only;
+  a.task_deg = B.d_tdeg; a.n_tasks = B.d_ntask;
+  a.kmax = B.d_kmax; a.nb = B.nb; a.spmmv_only = spmmv_only;
   void* args[] = {&a};
   const void* kf = filter_kernel_for(B.nb, B.ff);
   if (spmmv_only) {
@@ -825,6 +890,7 @@ fd_status enqueue_iteration(fd_ctx* ctx, Batch& B) {
   FD_CUDA(ctx, cudaMemcpyAsync(B.d_par, B.h_par, sizeof(BParams) * B.n, cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaMemcpyAsync(B.d_mu, B.h_mu, sizeof(double) * B.mu_cap, cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaMemcpyAsync(B.d_kmax, B.h_kmax, sizeof(int), cudaMemcpyHostToDevice, st));
+  FD_TRY(copy_tasks(ctx, B));
   const dim3 cgrid((unsigned)std::max(1, ctx->num_sms * 2), B.n);
   if (B.f32 || B.ff) {
     k_bconvert<<<cgrid, 256, 0, st>>>(B.d_inst, B.d_par, 1);
@@ -969,6 +1035,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
   // first iteration: no filter, orthonormalise + Rayleigh-Ritz
   for (int i = 0; i < n_inst; ++i) B.h_par[i] = BParams{1, 0, 0, 0, 0.0, 0.0, 0, 0};
   *B.h_kmax = 0;
+  B.list_tasks();
   // capture one iteration as a graph; replay it every outer iteration
   bool use_graph = true;
   cudaGraph_t graph = nullptr;
@@ -1084,6 +1151,7 @@ fd_status fd_solve_batched(fd_ctx* ctx, int n_inst, const fd_matrix* const* A,
       kmax = std::max(kmax, n);
     }
     *B.h_kmax = kmax;
+    B.list_tasks();
   }
   cudaEventRecord(e1, st);
   cudaEventSynchronize(e1);
@@ -1162,6 +1230,9 @@ fd_status fd_tune_batched(fd_ctx* ctx, int n_inst, const char* const* specs, int
         for (int k = 0; k <= probe_degree; ++k) mu[k] = 1.0 / (k + 1);
         std::copy(mu.begin(), mu.end(), B.h_mu);
         *B.h_kmax = probe_degree;
+        B.list_tasks();
+        s = copy_tasks(ctx, B);
+        if (s != FD_OK) { B.release(); break; }
         FD_CUDA(ctx, cudaMemcpyAsync(B.d_par, B.h_par, sizeof(BParams) * n_inst, cudaMemcpyHostToDevice, st));
         FD_CUDA(ctx, cudaMemcpyAsync(B.d_mu, B.h_mu, sizeof(double) * (probe_degree + 1), cudaMemcpyHostToDevice, st));
         FD_CUDA(ctx, cudaMemcpyAsync(B.d_kmax, B.h_kmax, sizeof(int), cudaMemcpyHostToDevice, st));
