@@ -53,9 +53,9 @@ FP64_TFLOPS = 1.25
 # capture of `bench.py --kernel-only f32` (profiles/k_cheb_step_f32_stencil_L128_nb64.md),
 # with the kernel shape it was taken on and the SHA-256 of the step kernel's sources
 # at that time: when the sources differ, the figure is stale and is reported as null
-TRAFFIC_F32 = {"bytes": 1.762259e9 + 1.027703e9, "kernel": "k_cheb_step<float,64,GENERIC>",
+TRAFFIC_F32 = {"bytes": 1.762372352e9 + 1.026334464e9, "kernel": "k_cheb_step<float,64,GENERIC>",
                "rows": 2097152, "nnz": 14680064, "nb": 64,
-               "sources_sha256": "07acd796f3c6df8ee3c9983fcae3522c5c496c4830eface00ef89088031c65fc"}
+               "sources_sha256": "2d8df2110905abb98dea013168e95e00ca44a068dc0340ac09f6f110cc395458"}
 STEP_SOURCES = ["paper_2209_01974_gb300/csrc/fd_step.cuh", "paper_2209_01974_gb300/csrc/fd_filter.cu"]
 
 

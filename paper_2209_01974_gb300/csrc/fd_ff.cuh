@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fd_step.cuh"
+
 namespace fdi {
 namespace ffa {
 
@@ -90,8 +92,6 @@ __device__ __forceinline__ ff ldg_val(const ff* p) {
 
 namespace step {
 
-template <typename T>
-struct V16;
 // two float-float values per 16-byte vector, each stored as (hi, lo)
 template <>
 struct V16<ffa::ff> {
@@ -121,6 +121,17 @@ struct V16<ffa::ff> {
     asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;\n"
                  :: "l"(p), "f"(t.x), "f"(t.y), "f"(t.z), "f"(t.w), "l"(pol));
   }
+};
+
+// Float-float steps run the FP32 shape: 4-warp CTAs, 12 per SM (<= 40
+// registers, no spills up to nb = 64).  Memory latency, not the FP32 pipes,
+// bounds the float-float step, and on the GB300 this shape (48 warps per SM)
+// took 1.41 ms per L = 128 stencil step at nb = 64 against 1.86 ms with the
+// FP64 shape (8-warp CTAs, 4 per SM).
+template <>
+struct StepShape<ffa::ff> {
+  static constexpr int warps = 4;
+  static constexpr int min_blocks = MIN_BLOCKS;
 };
 
 }  // namespace step

@@ -30,7 +30,7 @@ using namespace step;
 using ffa::ff;
 
 template <typename T, int NB, int MODE>
-__global__ void __launch_bounds__(step_warps<T>() * 32, sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64)
+__global__ void __launch_bounds__(step_warps<T>() * 32, step_min_blocks<T>())
     k_cheb_step(SellArgs<T> A, StepArgs<T> s, unsigned pf) {
   using L = Layout<T, NB>;
   constexpr int WARPS = step_warps<T>();
@@ -129,7 +129,7 @@ fd_status launch_step(fd_ctx* ctx, const fd_matrix* M, int mode, const StepArgs<
   const int64_t rows_per_block = (int64_t)SW * L::RPW;
   const unsigned grid = (unsigned)cdiv(M->D, rows_per_block);
   // prefetch distance: one wave of resident CTAs (the launch-bounds occupancy)
-  const unsigned pf = (unsigned)ctx->num_sms * (sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64);
+  const unsigned pf = (unsigned)ctx->num_sms * step_min_blocks<T>();
   if (mode == MODE_SPMMV) k_cheb_step<T, NB, MODE_SPMMV><<<grid, SW * 32, 0, ctx->stream>>>(A, s, pf);
   else if (mode == MODE_SECOND) k_cheb_step<T, NB, MODE_SECOND><<<grid, SW * 32, 0, ctx->stream>>>(A, s, pf);
   else k_cheb_step<T, NB, MODE_GENERIC><<<grid, SW * 32, 0, ctx->stream>>>(A, s, pf);

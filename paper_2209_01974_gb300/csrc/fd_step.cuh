@@ -128,10 +128,19 @@ constexpr int WARPS = 8;
 constexpr int BATCH = 4;   // entries per batch; SELL chunk lengths are multiples of 8
 constexpr int MIN_BLOCKS = 12;     // FP32 steps: 4-warp CTAs, 48 resident warps per SM (<= 40 registers)
 constexpr int MIN_BLOCKS_F64 = 4;  // FP64 steps: 8-warp CTAs with 64 registers (FP64-ALU bound anyway)
-// warps per CTA of the fused step (k_cheb_step): smaller CTAs for FP32 (more of
-// them in flight, a finer L2 prefetch granule), 8 for FP64
+// CTA shape of the fused step (k_cheb_step): warps per CTA and resident CTAs
+// per SM (the launch bounds).  Smaller CTAs for FP32 (more of them in flight, a
+// finer L2 prefetch granule), 8 warps for FP64; other arithmetic types may
+// specialise it.
 template <typename T>
-__host__ __device__ constexpr int step_warps() { return sizeof(T) == 4 ? 4 : WARPS; }
+struct StepShape {
+  static constexpr int warps = sizeof(T) == 4 ? 4 : WARPS;
+  static constexpr int min_blocks = sizeof(T) == 4 ? MIN_BLOCKS : MIN_BLOCKS_F64;
+};
+template <typename T>
+__host__ __device__ constexpr int step_warps() { return StepShape<T>::warps; }
+template <typename T>
+__host__ __device__ constexpr int step_min_blocks() { return StepShape<T>::min_blocks; }
 
 template <typename T, int NB>
 struct Layout {
