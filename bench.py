@@ -633,6 +633,11 @@ def run_batched(args):
     t0 = time.perf_counter()
     tune = fd.fd_tune_batched(ctx, specs, 16, 20)
     t_tune = time.perf_counter() - t0
+    if args.tune_only:  # the autotuner's probes alone (the profiling driver of k_batched_filter)
+        print(json.dumps({"phase": "tuner", "instances": n, "rows_total": sum(anderson_instance(s)[0] ** 3
+                                                                              for s in range(n)),
+                          "tuner": tune, "tuner_seconds": t_tune}))
+        return 0
     mats = [fd.fd_build_matrix(ctx, sp, C=tune["C"]) for sp in specs]
     nb = tune["nb"]
     ns = nb * -(-64 // nb)
@@ -797,6 +802,8 @@ def main():
                     help="--batched: finishing sweeps of the FP32 form (FP64 or float-float)")
     ap.add_argument("--learned", action="store_true", help="--batched: each instance's learned constants")
     ap.add_argument("--verbose", action="store_true", help="--batched / --tts: per-iteration log on stderr")
+    ap.add_argument("--tune-only", action="store_true",
+                    help="--batched: run the autotuner's probes and stop")
     ap.add_argument("--no-sequential", action="store_true",
                     help="--batched: time the batched solve only, not the one-by-one solves")
     ap.add_argument("--max-outer", type=int, default=40)
