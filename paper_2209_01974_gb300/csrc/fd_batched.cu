@@ -206,10 +206,14 @@ __device__ __forceinline__ void batched_row_group_ff(const BatchArgs& b, int t, 
   }
 }
 
-// FF: the instantiation with the float-float path, launched only by solves
-// that can use it (its extra registers then cost nothing elsewhere)
+// FF: the instantiation with FP32 and float-float rows only, the filter of
+// solves that use float-float sweeps.  It runs the shape of the
+// single-problem FP32 and float-float steps, 4-warp CTAs and 12 per SM
+// (48 warps, <= 40 registers): both are bound by memory latency.
+constexpr int BF_FF_WARPS = 4, BF_FF_BLOCKS = 12;
 template <int NB, bool FF>
-__global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
+__global__ void __launch_bounds__(FF ? BF_FF_WARPS * 32 : WARPS * 32, FF ? BF_FF_BLOCKS : 3)
+    k_batched_filter(BatchArgs b) {
   using L = Layout<double, NB>;
   extern __shared__ int64_t s_off[];  // n_tasks + 1 offsets, then n_tasks degrees
   const int nt = *b.n_tasks;
@@ -247,12 +251,13 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_batched_filter(BatchArgs b) {
         }
       }
       if constexpr (FF) {
-        if (!b.spmmv_only && b.par[inst].ff) {
-          batched_row_group_ff<NB>(b, lo, lrow0, k);
-          continue;
-        }
+        // a solve with float-float rows has no FP64 rows in its filter (every
+        // instance is FP32 or float-float; its Rayleigh-Ritz SpMMV runs in the
+        // other instantiation), so this one carries no FP64 path
+        batched_row_group_ff<NB>(b, lo, lrow0, k);
+      } else {
+        batched_row_group<NB>(b, lo, lrow0, k);
       }
-      batched_row_group<NB>(b, lo, lrow0, k);
     }
     if (!b.spmmv_only) grid.sync();
   }
@@ -642,6 +647,7 @@ struct Batch {
   int* h_kmax = nullptr;
   double* h_out = nullptr;  // theta and resid of all instances
   int grid = 0;
+  int grid_rr = 0, warps_rr = WARPS;  // the Rayleigh-Ritz SpMMV launch (FP64 rows)
   size_t smem_filter = 0;
   cudaGraphExec_t exec = nullptr;
   int64_t max_D = 0;
@@ -698,7 +704,7 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
                       int nb, int warps, size_t mu_cap, bool f32 = false, bool with_ff = false) {
   B.n = n;
   B.nb = nb;
-  B.warps = warps;
+  B.warps = with_ff ? BF_FF_WARPS : warps;  // the float-float instantiation's fixed shape
   B.f32 = f32;
   B.ff = with_ff;
   // rows per warp of the FP64 step; the FP32 step covers twice as many
@@ -800,9 +806,19 @@ fd_status batch_setup(fd_ctx* ctx, Batch& B, int n, const fd_matrix* const* A, c
   if (B.smem_filter > 48 * 1024)
     FD_CUDA(ctx, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem_filter));
   int per_sm = 0;
-  FD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, warps * 32, B.smem_filter));
+  FD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, B.warps * 32, B.smem_filter));
   if (per_sm < 1) return set_err(ctx, FD_ERR_ARG, "batched filter does not fit on an SM");
   B.grid = per_sm * ctx->num_sms;
+  // the SpMMV of the Rayleigh-Ritz step always takes FP64 rows: the FP64
+  // instantiation in the tuner's CTA shape
+  const void* kr = filter_kernel_for(nb, false);
+  B.warps_rr = warps;
+  if (B.smem_filter > 48 * 1024)
+    FD_CUDA(ctx, cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem_filter));
+  per_sm = 0;
+  FD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kr, B.warps_rr * 32, B.smem_filter));
+  if (per_sm < 1) return set_err(ctx, FD_ERR_ARG, "batched SpMMV does not fit on an SM");
+  B.grid_rr = per_sm * ctx->num_sms;
   return FD_OK;
 }
 
@@ -825,7 +841,8 @@ fd_status launch_filter(fd_ctx* ctx, Batch& B, int spmmv_only) {
   void* args[] = {&a};
   const void* kf = filter_kernel_for(B.nb, B.ff);
   if (spmmv_only) {
-    FD_CUDA(ctx, cudaLaunchKernel(kf, B.grid, B.warps * 32, args, B.smem_filter, ctx->stream));
+    FD_CUDA(ctx, cudaLaunchKernel(filter_kernel_for(B.nb, false), B.grid_rr, B.warps_rr * 32, args,
+                                  B.smem_filter, ctx->stream));
   } else {
     FD_CUDA(ctx, cudaLaunchCooperativeKernel(kf, B.grid, B.warps * 32, args, B.smem_filter, ctx->stream));
   }

@@ -121,3 +121,39 @@ def test_batched_fp32_form_needs_nb_4(fd, ctx):
     with pytest.raises(fd.FDError) as e:
         fd.fd_solve_batched(ctx, [A], [(-0.1, 0.1, 1, 0)], 2, 20, 1e-9, precision="f32")
     assert e.value.status == fd.FD_ERR_ARG
+
+
+@pytest.mark.parametrize("form", [{"precision": "ff"}, {"precision": "f32", "finish": "ff"}])
+def test_small_batch_ff_forms_match_dense(fd, ctx, form):
+    # float-float rows in the persistent batched filter (all sweeps, or the
+    # FP32 form's finish), the Rayleigh-Ritz SpMMV in the FP64 instantiation
+    mats = [fd.fd_build_matrix(ctx, s) for s in SMALL]
+    probs = [(-0.3, 0.3, 8, 0)] * 5 + [(7.5, 8.5, 8, 0)]
+    probs[4], probs[5] = (7.5, 8.5, 8, 0), (-0.3, 0.3, 8, 0)
+    out, res = fd.fd_solve_batched(ctx, mats, probs, 8, 40, 1e-9, **form)
+    for spec, (a, b, nt, _), (th, rho), r in zip(SMALL, probs, out, res):
+        ev = np.linalg.eigvalsh(mat.to_scipy(mat.build(spec)).toarray())
+        assert r["converged"] == 1, spec
+        assert rho.max() <= 1e-9, spec
+        assert np.abs(th - _nearest(ev, 0.5 * (a + b), nt)).max() <= 1e-10 * np.abs(ev).max(), spec
+    assert any(r["n_spmmv_ff"] > 0 for r in res)
+    if form["precision"] == "ff":
+        assert all(r["n_spmmv_f32"] == 0 for r in res)
+
+
+def test_uneven_anderson_batch_ff_finish_matches_sequential(fd, ctx):
+    # FP32 sweeps with the float-float finish, batched and one by one: the same
+    # switch rule and the same arithmetic per row, so the same eigenvalues
+    seeds = [0, 14, 22, 53]
+    specs = []
+    for s_ in seeds:
+        L, W = mat.anderson_instance(s_)
+        specs.append(f"anderson3d:L={L},W={float(W)!r},seed={s_}")
+    mats = [fd.fd_build_matrix(ctx, s_) for s_ in specs]
+    probs = [(-0.01, 0.01, 16, s_) for s_ in seeds]
+    out, res = fd.fd_solve_batched(ctx, mats, probs, 16, 200, 1e-9, precision="f32", finish="ff")
+    for m, (a, b, nt, sd), (th, rho), r in zip(mats, probs, out, res):
+        assert r["converged"] == 1 and rho.max() <= 1e-9
+        assert r["n_spmmv_ff"] > 0
+        th1, rho1, r1 = fd.fd_solve(ctx, m, a, b, nt, 16, 200, 1e-9, seed=sd, precision="f32", finish="ff")
+        assert np.abs(th - th1).max() <= 1e-10 * max(abs(r1["lam_l"]), abs(r1["lam_r"]))
