@@ -662,6 +662,7 @@ struct Batch {
     cudaFreeHost(h_task_p);
     cudaFreeHost(h_off_p);
     cudaFreeHost(h_tdeg_p);
+    cudaFreeHost(h_ntask);
   }
   // the tasks of the active instances, largest degree first (h_par's degrees)
   void list_tasks() {
