@@ -495,7 +495,7 @@ def time_to_solution(ctx, forms, spec=TTS_SPEC, nt=32, nb=32, half_width=0.002, 
 
 def config3_sweep(ctx, degree=50, reps=3):
     """The 14-site Hubbard ring (11,778,624 rows) fused step at nb = 32, 64, 128:
-    the matrix-free operator in FP32 and FP64, and the stored matrix in FP32;
+    the matrix-free operator in FP32, FP64 and float-float, and the stored matrix in FP32;
     per-step time of degree-`degree` filters and the step's algorithmic GB/s."""
     import torch
 
@@ -504,7 +504,8 @@ def config3_sweep(ctx, degree=50, reps=3):
     peak = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs")
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None) or 6800.0
     for label, spec, cases in (("kron", KERNEL_WORKLOADS["hubbard14kron"], [("f32", 32), ("f32", 64),
-                                                                          ("f32", 128), ("f64", 64)]),
+                                                                          ("f32", 128), ("f64", 64),
+                                                                          ("ff", 64)]),
                                ("stored", KERNEL_WORKLOADS["hubbard14"], [("f32", 64)])):
         A = fd.fd_build_matrix(ctx, spec)
         D, nnz = A.D, A.info["nnz"]
@@ -512,9 +513,13 @@ def config3_sweep(ctx, degree=50, reps=3):
         al, be = 2 / (hi - lo), -(hi + lo) / (hi - lo)
         mu = fd.fd_filter_coeffs(al * 9.0 + be, al * 9.5 + be, degree)
         for prec, nb in cases:
-            dt = torch.float64 if prec == "f64" else torch.float32
-            es = 8.0 if prec == "f64" else 4.0
+            dt = torch.float32 if prec == "f32" else torch.float64
+            es = 4.0 if prec == "f32" else 8.0
             V = torch.randn((D, nb), dtype=dt, device="cuda")
+            if prec == "ff":  # float-float pairs split from the FP64 block
+                Vff = torch.empty((D, nb, 2), dtype=torch.float32, device="cuda")
+                fd.fd_copy_block(ctx, V, Vff)
+                V = Vff
             W1, W2 = torch.empty_like(V), torch.empty_like(V)
             fd.fd_filter(ctx, A, V, mu, al, be, W1, W2)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

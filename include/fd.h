@@ -100,8 +100,10 @@ fd_status fd_set_workspace_limit(fd_ctx* ctx, size_t limit_bytes);
  *                                       kron=1 also builds the per-spin hopping
  *                                       tables: fd_filter and fd_spmmv then apply
  *                                       H = H_up x 1 + 1 x H_dn + U n_double without
- *                                       the stored matrix, with results equal to
- *                                       the stored-matrix kernel; needs sigma = 1)
+ *                                       the stored matrix: FP64 and float-float
+ *                                       rows summed in the stored order, FP32 in
+ *                                       column panels (equal to rounding); needs
+ *                                       sigma = 1)
  *   "anderson3d:L=128,W=2,seed=1,t=1"   periodic cubic lattice, eps_i = W (u_i - 1/2)
  *   "chain:n=1000,t=1"                  open tight-binding chain
  *   "roadgraph:side=2000,q=0.3,seed=0"  Laplacian of a road-like planar graph on a
@@ -173,8 +175,8 @@ fd_status fd_spectral_bounds(fd_ctx* ctx, const fd_matrix* A, int steps,
  *   prec    FD_F64: V, W1, W2 are double and H's FP64 values are used;
  *           FD_F32: V, W1, W2 are float, H's FP32 copy, FP32 accumulation;
  *           FD_FF: V, W1, W2 hold float-float pairs (2 floats per element,
- *           ld counted in elements), H's float-float copy of its FP64 values;
- *           stored matrices only (kron = 0 gives FD_ERR_ARG).
+ *           ld counted in elements), H's float-float copy of its FP64 values
+ *           (stored, or the matrix-free tables of kron = 1).
  *   nb      2, 4, 8, 16, 32, 64 or 128 (FP64, FF); 4 .. 128 (FP32)
  *   degree  n >= 2 (Alg. 2 takes degree n >= 2); mu: HOST array of n+1 doubles
  *   W1, W2  device workspaces, D x nb each with leading dimension ldw
@@ -311,7 +313,7 @@ typedef struct {
                         largest wanted residual reaches 100 u32 |H| or fails to
                         halve in two iterations in a row, then the finishing
                         sweeps of `finish`; FD_FF: all sweeps in float-float
-                        (stored matrices only) [FD_F64] */
+                        [FD_F64] */
   double c_n;        /* degree = c_n pi / dtheta [4] */
   double m_l, m_r;   /* window edge = target edge + m (search edge - target edge) [0.5] */
   int verbose;       /* 1: print one line per outer iteration to stderr */
@@ -333,7 +335,7 @@ typedef struct {
   int finish;        /* finishing sweeps of the FD_F32 form: FD_FINISH_F64
                         (FP64, the paper's FP64 sweeps) or FD_FINISH_FF
                         (float-float, FP64-like accuracy at FP32 arithmetic
-                        rates; stored matrices only) [FD_FINISH_F64] */
+                        rates) [FD_FINISH_F64] */
 } fd_options;
 
 enum { FD_FINISH_F64 = 0, FD_FINISH_FF = 1 };

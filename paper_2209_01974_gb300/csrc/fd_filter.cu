@@ -95,14 +95,18 @@ fd_status launch_kron_step(fd_ctx* ctx, const fd_matrix* M, int mode, const Step
   K.col_up = M->kcol[0];
   K.ptr_dn = M->kptr[1];
   K.col_dn = M->kcol[1];
-  if constexpr (sizeof(T) == 8) {
-    K.val_up = (const T*)M->kval[0];
-    K.val_dn = (const T*)M->kval[1];
-    K.diag = (const T*)M->kdiag;
+  if constexpr (std::is_same_v<T, double>) {
+    K.val_up = M->kval[0];
+    K.val_dn = M->kval[1];
+    K.diag = M->kdiag;
+  } else if constexpr (std::is_same_v<T, float>) {
+    K.val_up = M->kval32[0];
+    K.val_dn = M->kval32[1];
+    K.diag = M->kdiag32;
   } else {
-    K.val_up = (const T*)M->kval32[0];
-    K.val_dn = (const T*)M->kval32[1];
-    K.diag = (const T*)M->kdiag32;
+    K.val_up = reinterpret_cast<const ff*>(M->kvalff[0]);
+    K.val_dn = reinterpret_cast<const ff*>(M->kvalff[1]);
+    K.diag = reinterpret_cast<const ff*>(M->kdiagff);
   }
   const unsigned grid = (unsigned)cdiv(M->D, (int64_t)WARPS * L::RPW);
   if (mode == MODE_SPMMV) k_kron_step<T, NB, MODE_SPMMV><<<grid, WARPS * 32, 0, ctx->stream>>>(K, s);
@@ -114,11 +118,7 @@ fd_status launch_kron_step(fd_ctx* ctx, const fd_matrix* M, int mode, const Step
 
 template <typename T, int NB>
 fd_status launch_step(fd_ctx* ctx, const fd_matrix* M, int mode, const StepArgs<T>& s) {
-  if constexpr (std::is_same_v<T, ff>) {
-    if (M->kron) return set_err(ctx, FD_ERR_ARG, "float-float sweeps need a stored matrix (kron = 0)");
-  } else {
-    if (M->kron) return launch_kron_step<T, NB>(ctx, M, mode, s);
-  }
+  if (M->kron) return launch_kron_step<T, NB>(ctx, M, mode, s);
   using L = Layout<T, NB>;
   SellArgs<T> A;
   A.chunk_ptr = M->chunk_ptr; A.row_len = M->row_len; A.col = M->col; A.D = M->D; A.C = M->C;

@@ -56,12 +56,14 @@ struct fd_matrix {
   int kron = 0;
   double* kdiag = nullptr;          // 25: U * n for n doubly occupied sites
   float* kdiag32 = nullptr;         // 25: (float) (U * n)
+  float* kdiagff = nullptr;         // 25 float-float pairs of U * n
   int64_t kdim[2] = {0, 0};
   uint32_t* kbits[2] = {nullptr, nullptr};
   int64_t* kptr[2] = {nullptr, nullptr};   // kdim + 1
   int32_t* kcol[2] = {nullptr, nullptr};
   double* kval[2] = {nullptr, nullptr};
   float* kval32[2] = {nullptr, nullptr};
+  float* kvalff[2] = {nullptr, nullptr};  // float-float pairs of kval
   // Tables of the panel kernel of the matrix-free operator (fd_kron.cu):
   // korder: the up-spin states (slabs u) in reverse Cuthill-McKee order of the
   // up-spin hopping graph, the order in which a step visits the slabs;

@@ -837,17 +837,26 @@ static fd_status build_kron(fd_ctx* ctx, fd_matrix* A, const HubbardP& p) {
     k_kron_fill<<<(unsigned)cdiv(dim, T), T, 0, st>>>(p.L, N, p.periodic, p.t, dim, A->kptr[sp], A->kcol[sp],
                                                       A->kval[sp], A->kval32[sp]);
     FD_LAUNCHED(ctx);
+    FD_CUDA(ctx, cudaMalloc(&A->kvalff[sp], 2 * sizeof(float) * m));
+    if (nh > 0) {
+      k_split_ff<<<(unsigned)cdiv(nh, T), T, 0, st>>>(A->kval[sp], nh, A->kvalff[sp]);
+      FD_LAUNCHED(ctx);
+    }
   }
   double dg[25];
-  float dg32[25];
+  float dg32[25], dgff[50];
   for (int n = 0; n <= 24; ++n) {
     dg[n] = p.U * (double)n;  // the generator's U * popcount
     dg32[n] = (float)dg[n];   // as the FP32 copy of the stored values
+    dgff[2 * n] = dg32[n];    // and the float-float split of the FP64 value
+    dgff[2 * n + 1] = (float)(dg[n] - (double)dg32[n]);
   }
   FD_CUDA(ctx, cudaMalloc(&A->kdiag, sizeof(dg)));
   FD_CUDA(ctx, cudaMalloc(&A->kdiag32, sizeof(dg32)));
+  FD_CUDA(ctx, cudaMalloc(&A->kdiagff, sizeof(dgff)));
   FD_CUDA(ctx, cudaMemcpyAsync(A->kdiag, dg, sizeof(dg), cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaMemcpyAsync(A->kdiag32, dg32, sizeof(dg32), cudaMemcpyHostToDevice, st));
+  FD_CUDA(ctx, cudaMemcpyAsync(A->kdiagff, dgff, sizeof(dgff), cudaMemcpyHostToDevice, st));
   FD_CUDA(ctx, cudaStreamSynchronize(st));
   FD_TRY(kron_panel_tables(ctx, A, p.t));
   A->kron = 1;
@@ -1045,9 +1054,9 @@ fd_status fd_matrix_free(fd_matrix* A) {
   cudaFree(A->val32); cudaFree(A->valff); cudaFree(A->perm); cudaFree(A->iperm); cudaFree(A->diag_added);
   for (int sp = 0; sp < 2; ++sp) {
     cudaFree(A->kbits[sp]); cudaFree(A->kptr[sp]); cudaFree(A->kcol[sp]);
-    cudaFree(A->kval[sp]); cudaFree(A->kval32[sp]);
+    cudaFree(A->kval[sp]); cudaFree(A->kval32[sp]); cudaFree(A->kvalff[sp]);
   }
-  cudaFree(A->kdiag); cudaFree(A->kdiag32);
+  cudaFree(A->kdiag); cudaFree(A->kdiag32); cudaFree(A->kdiagff);
   cudaFree(A->korder); cudaFree(A->kdn_ptr); cudaFree(A->kdn_ent); cudaFree(A->kdn_ent16);
   delete A;
   return FD_OK;

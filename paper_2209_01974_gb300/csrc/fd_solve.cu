@@ -310,8 +310,6 @@ static fd_status solve_impl(fd_ctx* ctx, const fd_matrix* A, double a, double b,
   if (opt.precision == FD_F32 && nb < 4) return set_err(ctx, FD_ERR_ARG, "FP32 sweeps need nb >= 4");
   // float-float sweeps: the FD_FF form, or the FD_F32 form's finish
   const bool ff_sweeps = opt.precision == FD_FF || (opt.precision == FD_F32 && opt.finish == FD_FINISH_FF);
-  if (ff_sweeps && A && A->kron)
-    return set_err(ctx, FD_ERR_ARG, "float-float sweeps need a stored matrix (kron = 0)");
   if (degree < 2) return set_err(ctx, FD_ERR_ARG, "degree must be >= 2 (Alg. 2)");
   if (opt.intervals != FD_INTERVALS_RITZ && opt.intervals != FD_INTERVALS_LEHMANN)
     return set_err(ctx, FD_ERR_ARG, "intervals must be FD_INTERVALS_RITZ or FD_INTERVALS_LEHMANN");

@@ -115,15 +115,38 @@ def test_spmmv_ff_matches_oracle(fd, ctx, nb):
     assert np.all(np.abs(got - ref) <= bound)
 
 
-def test_ff_rejected_on_matrix_free(fd, ctx):
+@pytest.mark.parametrize("spec", ["hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open",
+                                  "hubbard:n_sites=7,n_up=3,n_dn=2,t=1,U=4.3,bc=periodic"])
+@pytest.mark.parametrize("nb", [2, 16])
+def test_filter_ff_matrix_free_matches_oracle(fd, ctx, spec, nb):
+    """The matrix-free Hubbard operator (kron=1) in float-float against the
+    oracle within the derived bound, and against the stored matrix's
+    float-float filter within twice it."""
     import torch
-    A = fd.fd_build_matrix(ctx, "hubbard:n_sites=6,n_up=3,n_dn=3,t=1,U=4,bc=periodic,kron=1")
-    V = torch.zeros((A.D, 4, 2), dtype=torch.float32, device="cuda")
-    W1, W2 = torch.empty_like(V), torch.empty_like(V)
-    with pytest.raises(fd.FDError):
-        fd.fd_filter(ctx, A, V, np.ones(3), 0.1, 0.0, W1, W2)
-    with pytest.raises(fd.FDError):
-        fd.fd_solve(ctx, A, -0.5, 0.5, 4, 4, 50, 1e-9, precision="ff")
+    csr = mat.build(spec)
+    D = len(csr[0]) - 1
+    V0 = fd_inputs.random_block(D, nb, 31 + nb)
+    mu, alpha, beta = _params(csr, 30)
+    out = []
+    for s_ in (spec + ",kron=1", spec):
+        A = fd.fd_build_matrix(ctx, s_)
+        V = _ff_block(fd, ctx, torch.from_numpy(V0).cuda())
+        W1, W2 = torch.empty_like(V), torch.empty_like(V)
+        fd.fd_filter(ctx, A, V, mu, alpha, beta, W1, W2)
+        out.append(_to_f64(fd, ctx, V))
+    ref = ch.cheb_filter(mat.to_scipy(csr), V0, mu, alpha, beta)
+    tol = filter_tolerance(csr, mu, alpha, beta, V0, U_FF)
+    assert np.all(np.abs(out[0] - ref) <= tol)
+    assert np.all(np.abs(out[0] - out[1]) <= 2 * tol)
+
+
+def test_solve_ff_finish_on_matrix_free(fd, ctx):
+    spec = "hubbard:n_sites=8,n_up=4,n_dn=4,t=1,U=4,bc=open"
+    A = fd.fd_build_matrix(ctx, spec + ",kron=1")
+    th0, r0, res0 = fd.fd_solve(ctx, fd.fd_build_matrix(ctx, spec), -0.5, 0.5, 20, 32, 100, 1e-9)
+    th, r, res = fd.fd_solve(ctx, A, -0.5, 0.5, 20, 32, 100, 1e-9, precision="f32", finish="ff")
+    assert res["converged"] and np.all(r <= 1e-9) and res["n_spmmv_ff"] > 0
+    assert np.abs(np.sort(th) - np.sort(th0)).max() <= 1e-10 * max(1.0, np.abs(th0).max())
 
 
 @pytest.mark.parametrize("form", [{"precision": "ff"}, {"precision": "f32", "finish": "ff"}])
