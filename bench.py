@@ -53,9 +53,9 @@ FP64_TFLOPS = 1.25
 # capture of `bench.py --kernel-only f32` (profiles/k_cheb_step_f32_stencil_L128_nb64.md),
 # with the kernel shape it was taken on and the SHA-256 of the step kernel's sources
 # at that time: when the sources differ, the figure is stale and is reported as null
-TRAFFIC_F32 = {"bytes": 1.762372352e9 + 1.026334464e9, "kernel": "k_cheb_step<float,64,GENERIC>",
+TRAFFIC_F32 = {"bytes": 1.762341888e9 + 1.0270528e9, "kernel": "k_cheb_step<float,64,GENERIC>",
                "rows": 2097152, "nnz": 14680064, "nb": 64,
-               "sources_sha256": "2d8df2110905abb98dea013168e95e00ca44a068dc0340ac09f6f110cc395458"}
+               "sources_sha256": "ca2c354e272c5d65b724693c96f91916002584102c602b2b76fa213a5c67b8c7"}
 STEP_SOURCES = ["paper_2209_01974_gb300/csrc/fd_step.cuh", "paper_2209_01974_gb300/csrc/fd_filter.cu"]
 
 
